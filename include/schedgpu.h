@@ -1,0 +1,258 @@
+/*
+ * schedgpu.h -- C ABI of a memory-safe GPU co-scheduler for one B300
+ * (sm_103a), following the life cycle of schedGPU (arXiv 1712.04495,
+ * Sec. II and Sec. IV): initialise, pre-allocate (declare a device-memory
+ * need and wait for the grant), run, post-free (release), shut down.
+ *
+ * Conventions for every call:
+ *   - Return value: SG_OK (0) or one of the SG_* error codes below; nothing
+ *     aborts the process. sg_strerror() names a code.
+ *   - Pointers are plain host or device addresses as stated per argument;
+ *     sizes are bytes unless named otherwise. Streams are cudaStream_t
+ *     handles passed as void* (NULL = the legacy default stream).
+ *   - The library never allocates device memory after sg_init(); the pool
+ *     belongs to the caller and must outlive the context.
+ *   - Calls on one context are safe from several host threads (the paper's
+ *     "clients" are threads of one process here).
+ */
+#ifndef SCHEDGPU_H
+#define SCHEDGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ codes */
+/* Error codes mirror the CUDA codes the paper's API returns (Sec. IV):
+ * cudaSuccess -> SG_OK, cudaErrorNotReady -> SG_NOT_READY (non-blocking
+ * pre-allocation that cannot be served), cudaErrorUnknown -> SG_ERR_UNKNOWN. */
+#define SG_OK             0
+#define SG_NOT_READY      1  /* request queued, not granted yet                  */
+#define SG_ERR_TIMEOUT    2  /* blocking wait expired; the ticket is withdrawn   */
+#define SG_ERR_TOO_LARGE  3  /* need exceeds the whole pool; never queued        */
+#define SG_ERR_INVALID    4  /* bad argument, unknown ticket, double release     */
+#define SG_ERR_CUDA       5  /* a CUDA runtime call or launch failed             */
+#define SG_ERR_UNKNOWN    6  /* internal error                                   */
+#define SG_ERR_CAPACITY   7  /* ticket table of the context is full              */
+#define SG_ERR_DEVICE     8  /* the device engine raised an error flag           */
+
+/* Notification policies of Sec. V. A smaller priority value is a higher
+ * priority (the priority argument of the paper's initialisation call). */
+#define SG_POLICY_FIFO            0  /* Policy 1: serve the head while it fits      */
+#define SG_POLICY_FIRST_FIT       1  /* Policy 2, MMU: serve every waiter that fits */
+#define SG_POLICY_PRIO_FIFO       2  /* Policy 3: FIFO over (priority, arrival)     */
+#define SG_POLICY_PRIO_FIRST_FIT  3  /* Policy 4: first fit in the top class        */
+
+/* sg_config.flags */
+#define SG_FLAG_FIFO_BYPASS  1u  /* FIFO: an arrival that fits is served even if
+                                    others wait (the literal Sec. IV check)      */
+
+/* Ticket / job states (sg_record.status). */
+#define SG_ST_PENDING    0
+#define SG_ST_QUEUED     1
+#define SG_ST_RUNNING    2   /* granted, memory held */
+#define SG_ST_DONE       3   /* released             */
+#define SG_ST_TIMEOUT    4
+#define SG_ST_TOO_LARGE  5
+
+/* Job kinds run by sg_launch / sg_run_trace. */
+#define SG_KIND_TRIAD 0      /* FP32 STREAM triad a = b + 3 c              */
+#define SG_KIND_SPMV  1      /* FP32 CSR SpMV y = A x                      */
+#define SG_KIND_GEMM  2      /* BF16 GEMM C = A B^T, FP32 accumulation     */
+
+/* sg_run_trace.mode */
+#define SG_RUN_SATURATED  1u  /* every job arrives at t = 0                        */
+#define SG_RUN_TIMED      2u  /* jobs arrive at their arrival_ns (host clock)      */
+#define SG_RUN_EXCLUSIVE  4u  /* each job declares the whole pool (one at a time)  */
+#define SG_RUN_HOST_IO    8u  /* jobs / log / keep are HOST buffers, copied inside */
+#define SG_RUN_KEEP      16u  /* write a digest of each job's output before release */
+
+/* One job of a trace: 64 bytes, little-endian, no padding. The layout of a
+ * job's data inside its grant and the generator of its inputs are fixed by
+ * the kind (see sg_gen_* below). */
+typedef struct sg_job {
+    uint64_t arrival_ns;   /* arrival time on the trace clock              */
+    uint64_t need;         /* declared bytes (rounded up to the granule)   */
+    uint64_t duration_ns;  /* declared duration: the replay clock only     */
+    uint64_t timeout_ns;   /* UINT64_MAX = wait forever; 0 = non-blocking  */
+    uint64_t key;          /* SplitMix64 key of the job's data             */
+    uint64_t p0;           /* triad n | spmv rows | gemm M                 */
+    uint64_t p1;           /* spmv nnz capacity | gemm N                   */
+    uint32_t p2;           /* spmv Poisson table index | gemm K            */
+    uint16_t kind;         /* SG_KIND_*                                    */
+    int16_t  prio;         /* smaller = higher priority                    */
+} sg_job;
+
+/* Per-ticket log entry: 48 bytes. Times are the trace clock (replay) or
+ * %globaltimer ns (real runs). */
+typedef struct sg_record {
+    int32_t  status;       /* SG_ST_*                                      */
+    int32_t  slot;         /* real runs: stream slot the job ran on, else -1 */
+    int64_t  grant_seq;    /* order of grants, -1 if never granted         */
+    uint64_t grant_t;
+    uint64_t offset;       /* byte offset of the grant in the pool         */
+    uint64_t done_t;       /* release time (or timeout time)               */
+    uint64_t arrival_t;
+} sg_record;
+
+typedef struct sg_config {
+    uint32_t policy;       /* SG_POLICY_*                                  */
+    uint32_t flags;        /* SG_FLAG_*                                    */
+    uint32_t max_tickets;  /* capacity of the ticket table (0 = 1 << 17)   */
+    uint32_t n_streams;    /* stream slots for sg_run_trace (0 = 48)       */
+    uint64_t granule;      /* allocation granule, power of two >= 256 (0 = 256) */
+} sg_config;
+
+typedef struct sg_grant {
+    uint64_t offset;       /* byte offset in the pool                      */
+    void*    ptr;          /* device pointer = pool + offset; valid until release */
+    uint64_t grant_time_ns;
+} sg_grant;
+
+typedef struct sg_ctx sg_ctx;
+typedef uint32_t sg_ticket;
+
+typedef struct sg_run_stats {
+    uint64_t elapsed_ns;       /* CUDA-event time from first declare to last release */
+    uint64_t makespan_ns;      /* last release - first arrival (device clock)  */
+    uint64_t wait_p50_ns, wait_p99_ns;             /* grant - arrival, nearest rank */
+    uint64_t turnaround_p50_ns, turnaround_p99_ns; /* release - arrival           */
+    uint64_t peak_used;        /* peak granted bytes                           */
+    uint64_t frag_waits;       /* count-fit requests that could not be placed  */
+    uint64_t launches;         /* kernels this call launched                   */
+    uint64_t passes;           /* notification passes run by the engine        */
+    uint32_t jobs_done, jobs_failed;
+} sg_run_stats;
+
+/* ------------------------------------------------------- life cycle */
+/* Initialisation (Sec. IV, the paper's schedGPUInit). Creates a context
+ * whose engine state -- budget, used bytes, per-ticket grants, the wait
+ * queue and the free-extent list: the shared data of Sec. III-B -- lives in
+ * device memory allocated here, once. dev_pool: device pointer, 256-byte
+ * aligned, pool_bytes long, owned by the caller. cfg may be NULL for
+ * defaults. *out receives the context. Errors: SG_ERR_INVALID
+ * (null/misaligned pool, bad config), SG_ERR_CUDA. */
+int sg_init(sg_ctx** out, void* dev_pool, uint64_t pool_bytes, const sg_config* cfg);
+
+/* Shutdown (Sec. IV): waits for the context's streams, releases every
+ * ticket still holding memory (notifying waiters), and frees the context
+ * (never the pool). */
+int sg_shutdown(sg_ctx* ctx);
+
+/* Forget every ticket and return the pool to one free extent. Only valid
+ * when no job of the context is in flight. Synchronous. */
+int sg_reset(sg_ctx* ctx);
+
+/* Pre-allocation, first half (Sec. IV, preCudaMalloc): declare a need of
+ * `need` bytes with `priority`; the device engine queues the request and
+ * runs the admission pass. A grant never notifies other waiters.
+ * Returns SG_OK with *out set (the request may already be granted; check
+ * with sg_try), SG_ERR_TOO_LARGE at once if the need exceeds the pool,
+ * SG_ERR_CAPACITY if the ticket table is full. */
+int sg_declare(sg_ctx* ctx, uint64_t need, int32_t priority, sg_ticket* out);
+
+/* Non-blocking check (Sec. IV: a non-blocking pre-allocation returns
+ * cudaErrorNotReady): SG_OK and *out filled if granted, SG_NOT_READY if
+ * still queued, SG_ERR_TIMEOUT if withdrawn, SG_ERR_INVALID otherwise. */
+int sg_try(sg_ctx* ctx, sg_ticket t, sg_grant* out);
+
+/* Blocking pre-allocation bounded by timeout_ns (Sec. IV and its footnote:
+ * a timeout avoids deadlock). On expiry the ticket is withdrawn from the
+ * device queue (which re-runs the notification pass) and SG_ERR_TIMEOUT is
+ * returned -- unless the grant won the race, then SG_OK. */
+int sg_wait(sg_ctx* ctx, sg_ticket t, uint64_t timeout_ns, sg_grant* out);
+
+/* Post-free (Sec. IV, postCudaFree): enqueue on `stream`, after the work
+ * that uses the memory, the release of `bytes` declared bytes of ticket t
+ * (0 = everything it holds, the paper's bytes == 0 form; a smaller amount
+ * shrinks the grant from its end). Freeing notifies the waiters through
+ * the policy pass on the device. SG_ERR_INVALID if t holds no memory (the
+ * paper's check that the bytes were pre-allocated). */
+int sg_release(sg_ctx* ctx, sg_ticket t, uint64_t bytes, void* stream);
+
+/* Run job `job` in the memory granted to ticket t, on `stream`: its input
+ * generator, then its kernel, whose last block releases the ticket
+ * (wake-on-release without a host round trip). tables_dev: device array of
+ * 64-entry uint64 Poisson tables (SpMV jobs), may be NULL otherwise. */
+int sg_launch(sg_ctx* ctx, sg_ticket t, const sg_job* job, const uint64_t* tables_dev,
+              void* stream);
+
+/* Run a whole trace: declare every job (at t=0 or at its arrival time),
+ * launch each as it is granted on a free stream slot, until every job is
+ * released. Ticket i is job i. jobs/log: device buffers (host buffers with
+ * SG_RUN_HOST_IO, copied in and out inside the call). log receives one
+ * sg_record per job (device clock). keep (SG_RUN_KEEP): n uint64 output
+ * digests (see sg_digest), else NULL. stats may be NULL. */
+int sg_run_trace(sg_ctx* ctx, const sg_job* jobs, uint32_t n, const uint64_t* tables_dev,
+                 uint32_t mode, sg_record* log, uint64_t* keep, sg_run_stats* stats);
+
+/* Replay a trace on the device engine with the logical clock and declared
+ * durations (no job runs): the admission log the oracle must reproduce bit
+ * for bit. jobs_dev sorted by arrival_ns (ties by index); log_dev receives n
+ * records; workspace_dev of sg_replay_workspace_bytes(n) bytes, owned by
+ * the caller. One warp runs the whole event loop on `stream`. stats_dev:
+ * 4 uint64 (peak_used, frag_waits, passes, error flags) or NULL. */
+uint64_t sg_replay_workspace_bytes(uint32_t n);
+int sg_replay(const sg_job* jobs_dev, uint32_t n, uint64_t budget, uint64_t granule,
+              uint32_t policy, uint32_t flags, uint32_t exclusive, sg_record* log_dev,
+              void* workspace_dev, uint64_t* stats_dev, void* stream);
+
+/* Flags raised by job kernels that gave up a bounded wait (the tcgen05
+ * GEMM's mbarrier waits), OR-ed since the last call, then cleared.
+ * Synchronous (device-wide). */
+int sg_kernel_errors(uint32_t* flags_out);
+
+/* Engine error flags of the context (0 = none). */
+uint32_t sg_device_error(sg_ctx* ctx);
+const char* sg_strerror(int code);
+
+/* ------------------------------------------------------ job kernels */
+/* FP32 STREAM triad a[i] = b[i] + s*c[i], product and sum rounded
+ * separately (no fused multiply-add). Device pointers, n elements;
+ * 128-bit access when all three are 16-byte aligned. */
+int sg_triad(float* a, const float* b, const float* c, float s, uint64_t n, void* stream);
+
+/* Triad inputs of a job with data key `key`: b = U(stream 1), c = U(stream 2)
+ * where U is uniform[-1,1) from SplitMix64 (tracegen's element generator). */
+int sg_gen_triad(float* b, float* c, uint64_t n, uint64_t key, void* stream);
+
+/* FP32 CSR SpMV y = A x. row_ptr: rows+1 entries, int32 (ptr64 = 0) or
+ * int64 (ptr64 = 1); col int32, val fp32 (nnz each); x, y fp32 (rows).
+ * Square matrix; device pointers. */
+int sg_spmv(const void* row_ptr, int ptr64, const int32_t* col, const float* val,
+            const float* x, float* y, uint64_t rows, void* stream);
+
+/* Build the CSR matrix and x of an SpMV job in its declared layout at
+ * `base` (row_ptr, col, val, x, y, scan workspace; each 256-byte aligned;
+ * col / val sized for nnz_cap entries, row_ptr int64 when nnz_cap >= 2^31):
+ * row lengths by inverse CDF on table_dev (64 uint64 thresholds), columns
+ * uniform in [0, rows), values N(0,1), x uniform[-1,1). If the generated
+ * row lengths sum to more than nnz_cap, row_ptr is clamped to nnz_cap and
+ * a flag is OR-ed into err_dev (uint32, may be NULL). The scan workspace is
+ * scratch inside the layout. */
+int sg_gen_spmv(void* base, uint64_t rows, uint64_t nnz_cap, const uint64_t* table_dev,
+                uint64_t key, uint32_t* err_dev, void* stream);
+
+/* BF16 GEMM on tcgen05 tensor cores: C[M x N] (fp32, row-major) =
+ * A[M x K] (bf16, row-major) * B, with B given transposed as Bt[N x K]
+ * (bf16, row-major, K contiguous). M and N multiples of 128, K a multiple
+ * of 64 (else SG_ERR_INVALID); pointers 16-byte aligned. */
+int sg_gemm_bf16(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, uint32_t N,
+                 uint32_t K, void* stream);
+
+/* GEMM inputs: A[i,k] = bf16(U(stream 1, i*K+k)), Bt[j,k] = bf16(U(stream 2, j*K+k)). */
+int sg_gen_gemm(uint16_t* A, uint16_t* Bt, uint32_t M, uint32_t N, uint32_t K, uint64_t key,
+                void* stream);
+
+/* Order-independent 64-bit digest of `words` 32-bit words at dev_ptr:
+ * sum over i of mix64((i << 32) | word_i), modulo 2^64, added into
+ * *out_dev (device uint64). Equal outputs give equal digests. */
+int sg_digest(const void* dev_ptr, uint64_t words, uint64_t* out_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCHEDGPU_H */

@@ -1,0 +1,226 @@
+"""ctypes binding of ``libschedgpu.so``: the C ABI of ``include/schedgpu.h``
+under the same names, argument marshalling only.
+
+Every step of the co-scheduler runs in the library's CUDA kernels; nothing
+here computes, schedules or falls back to the CPU. Loading fails loudly if
+the library is missing (build it with ``paper_1712_04495_b300.build``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import tracegen as _tg
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libschedgpu.so")
+
+SG_OK, SG_NOT_READY, SG_ERR_TIMEOUT, SG_ERR_TOO_LARGE, SG_ERR_INVALID, SG_ERR_CUDA, \
+    SG_ERR_UNKNOWN, SG_ERR_CAPACITY, SG_ERR_DEVICE = range(9)
+SG_POLICY_FIFO, SG_POLICY_FIRST_FIT, SG_POLICY_PRIO_FIFO, SG_POLICY_PRIO_FIRST_FIT = range(4)
+POLICIES = {"fifo": 0, "first_fit": 1, "mmu": 1, "prio_fifo": 2, "prio_first_fit": 3, "prio_mmu": 3}
+SG_FLAG_FIFO_BYPASS = 1
+SG_ST_PENDING, SG_ST_QUEUED, SG_ST_RUNNING, SG_ST_DONE, SG_ST_TIMEOUT, SG_ST_TOO_LARGE = range(6)
+SG_RUN_SATURATED, SG_RUN_TIMED, SG_RUN_EXCLUSIVE, SG_RUN_HOST_IO, SG_RUN_KEEP = 1, 2, 4, 8, 16
+
+JOB_DTYPE = _tg.JOB_DTYPE
+RECORD_DTYPE = np.dtype([("status", "<i4"), ("slot", "<i4"), ("grant_seq", "<i8"),
+                         ("grant_t", "<u8"), ("offset", "<u8"), ("done_t", "<u8"),
+                         ("arrival_t", "<u8")])
+assert RECORD_DTYPE.itemsize == 48
+
+
+class SgConfig(ctypes.Structure):
+    _fields_ = [("policy", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("max_tickets", ctypes.c_uint32), ("n_streams", ctypes.c_uint32),
+                ("granule", ctypes.c_uint64)]
+
+
+class SgGrant(ctypes.Structure):
+    _fields_ = [("offset", ctypes.c_uint64), ("ptr", ctypes.c_void_p),
+                ("grant_time_ns", ctypes.c_uint64)]
+
+
+class SgRunStats(ctypes.Structure):
+    _fields_ = [("elapsed_ns", ctypes.c_uint64), ("makespan_ns", ctypes.c_uint64),
+                ("wait_p50_ns", ctypes.c_uint64), ("wait_p99_ns", ctypes.c_uint64),
+                ("turnaround_p50_ns", ctypes.c_uint64), ("turnaround_p99_ns", ctypes.c_uint64),
+                ("peak_used", ctypes.c_uint64), ("frag_waits", ctypes.c_uint64),
+                ("launches", ctypes.c_uint64), ("passes", ctypes.c_uint64),
+                ("jobs_done", ctypes.c_uint32), ("jobs_failed", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class SgError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {sg_strerror(code)} (code {code})")
+        self.code = code
+
+
+_P = ctypes.c_void_p
+_U64 = ctypes.c_uint64
+_U32 = ctypes.c_uint32
+_I32 = ctypes.c_int32
+
+_SIGS = {
+    "sg_init": ([ctypes.POINTER(_P), _P, _U64, ctypes.POINTER(SgConfig)], ctypes.c_int),
+    "sg_shutdown": ([_P], ctypes.c_int),
+    "sg_reset": ([_P], ctypes.c_int),
+    "sg_declare": ([_P, _U64, _I32, ctypes.POINTER(_U32)], ctypes.c_int),
+    "sg_try": ([_P, _U32, ctypes.POINTER(SgGrant)], ctypes.c_int),
+    "sg_wait": ([_P, _U32, _U64, ctypes.POINTER(SgGrant)], ctypes.c_int),
+    "sg_release": ([_P, _U32, _U64, _P], ctypes.c_int),
+    "sg_launch": ([_P, _U32, _P, _P, _P], ctypes.c_int),
+    "sg_run_trace": ([_P, _P, _U32, _P, _U32, _P, _P, ctypes.POINTER(SgRunStats)], ctypes.c_int),
+    "sg_replay_workspace_bytes": ([_U32], _U64),
+    "sg_replay": ([_P, _U32, _U64, _U64, _U32, _U32, _U32, _P, _P, _P, _P], ctypes.c_int),
+    "sg_kernel_errors": ([ctypes.POINTER(_U32)], ctypes.c_int),
+    "sg_device_error": ([_P], _U32),
+    "sg_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    "sg_triad": ([_P, _P, _P, ctypes.c_float, _U64, _P], ctypes.c_int),
+    "sg_gen_triad": ([_P, _P, _U64, _U64, _P], ctypes.c_int),
+    "sg_spmv": ([_P, ctypes.c_int, _P, _P, _P, _P, _U64, _P], ctypes.c_int),
+    "sg_gen_spmv": ([_P, _U64, _U64, _P, _U64, _P, _P], ctypes.c_int),
+    "sg_gemm_bf16": ([_P, _P, _P, _U32, _U32, _U32, _P], ctypes.c_int),
+    "sg_gen_gemm": ([_P, _P, _U32, _U32, _U32, _U64, _P], ctypes.c_int),
+    "sg_digest": ([_P, _U64, _P, _P], ctypes.c_int),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_1712_04495_b300.build` (no CPU fallback exists)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(rc: int, what: str, ok=(SG_OK,)):
+    if rc not in ok:
+        raise SgError(rc, what)
+    return rc
+
+
+def sg_strerror(code: int) -> str:
+    return lib().sg_strerror(code).decode()
+
+
+# ------------------------------------------------------------- life cycle
+def sg_init(pool_ptr: int, pool_bytes: int, policy=0, flags=0, max_tickets=0, n_streams=0,
+            granule=0) -> int:
+    pol = POLICIES[policy] if isinstance(policy, str) else int(policy)
+    cfg = SgConfig(pol, flags, max_tickets, n_streams, granule)
+    out = _P()
+    _check(lib().sg_init(ctypes.byref(out), pool_ptr, pool_bytes, ctypes.byref(cfg)), "sg_init")
+    return out.value
+
+
+def sg_shutdown(ctx: int):
+    _check(lib().sg_shutdown(ctx), "sg_shutdown")
+
+
+def sg_reset(ctx: int):
+    _check(lib().sg_reset(ctx), "sg_reset")
+
+
+def sg_declare(ctx: int, need: int, priority: int = 0) -> int:
+    t = _U32()
+    _check(lib().sg_declare(ctx, need, priority, ctypes.byref(t)), "sg_declare")
+    return t.value
+
+
+def sg_try(ctx: int, ticket: int):
+    """(code, grant or None): SG_OK, SG_NOT_READY, SG_ERR_TIMEOUT, ..."""
+    g = SgGrant()
+    rc = lib().sg_try(ctx, ticket, ctypes.byref(g))
+    return rc, (g if rc == SG_OK else None)
+
+
+def sg_wait(ctx: int, ticket: int, timeout_ns: int):
+    g = SgGrant()
+    rc = lib().sg_wait(ctx, ticket, timeout_ns, ctypes.byref(g))
+    return rc, (g if rc == SG_OK else None)
+
+
+def sg_release(ctx: int, ticket: int, nbytes: int = 0, stream: int = 0) -> int:
+    return lib().sg_release(ctx, ticket, nbytes, stream)
+
+
+def sg_launch(ctx: int, ticket: int, job: np.ndarray, tables_ptr: int = 0, stream: int = 0) -> int:
+    job = np.ascontiguousarray(job, dtype=JOB_DTYPE).reshape(1)
+    return lib().sg_launch(ctx, ticket, job.ctypes.data, tables_ptr or None, stream)
+
+
+def sg_run_trace(ctx: int, jobs_ptr: int, n: int, tables_ptr: int, mode: int, log_ptr: int,
+                 keep_ptr: int = 0):
+    st = SgRunStats()
+    rc = lib().sg_run_trace(ctx, jobs_ptr, n, tables_ptr or None, mode, log_ptr or None,
+                            keep_ptr or None, ctypes.byref(st))
+    return rc, st.as_dict()
+
+
+def sg_replay_workspace_bytes(n: int) -> int:
+    return lib().sg_replay_workspace_bytes(n)
+
+
+def sg_replay(jobs_ptr: int, n: int, budget: int, granule: int, policy, flags: int, exclusive: bool,
+              log_ptr: int, ws_ptr: int, stats_ptr: int = 0, stream: int = 0) -> int:
+    pol = POLICIES[policy] if isinstance(policy, str) else int(policy)
+    return lib().sg_replay(jobs_ptr, n, budget, granule, pol, flags, int(bool(exclusive)), log_ptr,
+                           ws_ptr, stats_ptr or None, stream)
+
+
+def sg_kernel_errors() -> int:
+    v = _U32()
+    _check(lib().sg_kernel_errors(ctypes.byref(v)), "sg_kernel_errors")
+    return v.value
+
+
+def sg_device_error(ctx: int) -> int:
+    return lib().sg_device_error(ctx)
+
+
+# ----------------------------------------------------------------- kernels
+def sg_triad(a, b, c, s: float, n: int, stream: int = 0) -> int:
+    return lib().sg_triad(a, b, c, s, n, stream)
+
+
+def sg_gen_triad(b, c, n: int, key: int, stream: int = 0) -> int:
+    return lib().sg_gen_triad(b, c, n, key, stream)
+
+
+def sg_spmv(row_ptr, ptr64: bool, col, val, x, y, rows: int, stream: int = 0) -> int:
+    return lib().sg_spmv(row_ptr, int(ptr64), col, val, x, y, rows, stream)
+
+
+def sg_gen_spmv(base, rows: int, nnz: int, table_ptr, key: int, err_ptr=0, stream: int = 0) -> int:
+    return lib().sg_gen_spmv(base, rows, nnz, table_ptr, key, err_ptr or None, stream)
+
+
+def sg_gemm_bf16(A, Bt, C, M: int, N: int, K: int, stream: int = 0) -> int:
+    return lib().sg_gemm_bf16(A, Bt, C, M, N, K, stream)
+
+
+def sg_gen_gemm(A, Bt, M: int, N: int, K: int, key: int, stream: int = 0) -> int:
+    return lib().sg_gen_gemm(A, Bt, M, N, K, key, stream)
+
+
+def sg_digest(ptr, words: int, out_ptr, stream: int = 0) -> int:
+    return lib().sg_digest(ptr, words, out_ptr, stream)

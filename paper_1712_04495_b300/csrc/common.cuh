@@ -1,0 +1,69 @@
+// Shared device helpers: SplitMix64 element generator, clock, cache-global
+// memory access. No scheduling logic here.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "../../include/schedgpu.h"
+
+#define SG_FULL 0xffffffffu
+
+namespace sg {
+
+// SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): output i of the stream
+// seeded with state k is mix64(k + (i + 1) * GAMMA).
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t sm64_at(uint64_t key, uint64_t i) {
+  return mix64(key + (i + 1) * kGamma);
+}
+// key of data stream s of a job with key k
+__host__ __device__ __forceinline__ uint64_t stream_key(uint64_t k, uint64_t s) {
+  return sm64_at(k, s);
+}
+
+// uniform[-1, 1): 24 high bits scaled by 2^-23, minus one; exact in fp32
+__device__ __forceinline__ float uniform_pm1(uint64_t h) {
+  return __fsub_rn(__fmul_rn((float)(uint32_t)(h >> 40), 0x1p-23f), 1.0f);
+}
+
+// N(0,1) by Box-Muller on two 24-bit uniforms taken from one hash
+__device__ __forceinline__ float normal01(uint64_t h) {
+  float u1 = (float)((uint32_t)(h >> 40) + 1u) * 0x1p-24f;            // (0, 1]
+  float u2 = (float)((uint32_t)(h >> 16) & 0xFFFFFFu) * 0x1p-24f;     // [0, 1)
+  return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+}
+
+// column index in [0, n): multiply-shift of the high 32 bits
+__device__ __forceinline__ uint32_t column_of(uint64_t h, uint64_t n) {
+  return (uint32_t)(((h >> 32) * n) >> 32);
+}
+
+// bf16 bits of an fp32 value, round to nearest, ties to even (finite input)
+__device__ __forceinline__ uint32_t bf16_rne_bits(float x) {
+  uint32_t b = __float_as_uint(x);
+  b += 0x7FFFu + ((b >> 16) & 1u);
+  return b >> 16;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+// L2-coherent accesses for state shared by concurrently running kernels
+template <typename T>
+__device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
+template <typename T>
+__device__ __forceinline__ void stcg(T* p, T v) { __stcg(p, v); }
+
+}  // namespace sg

@@ -1,0 +1,657 @@
+// Host runtime of the co-scheduler and the engine's kernels.
+//
+// The engine state (Sec. III-B shared data) is device memory allocated once
+// in sg_init. Every life-cycle call of Sec. IV becomes a one-warp control
+// kernel that takes the device lock, runs the operation and its policy pass
+// (Sec. V), and publishes the resulting grants through host-mapped memory:
+// a per-ticket record whose status word is written last, and a ring of
+// granted tickets -- the in-process stand-in for the paper's signal to a
+// waiting client. Jobs launched by the library release their ticket from
+// the last block of their final kernel, so wake-on-release needs no host
+// round trip.
+#include <algorithm>
+#include <chrono>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "engine.cuh"
+#include "jobs.h"
+
+using namespace sg;
+
+namespace {
+
+// ------------------------------------------------------------- kernels
+__device__ __forceinline__ uint64_t round_need(uint64_t need, uint64_t granule) {
+  uint64_t g = (need + granule - 1) / granule * granule;
+  return g == 0 ? granule : g;
+}
+
+__global__ void k_eng_reset(Eng E, uint64_t budget, uint64_t granule, uint32_t policy, uint32_t flags,
+                            uint32_t cap) {
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = tid; i < cap; i += stride) {
+    E.status[i] = ST_PENDING;
+    E.blk_done[i] = 0;
+  }
+  if (tid == 0) {
+    EngHdr* h = E.hdr;
+    h->budget = budget;
+    h->granule = granule;
+    h->used = 0;
+    h->seq = 0;
+    h->peak_used = 0;
+    h->frag_waits = 0;
+    h->passes = 0;
+    h->policy = policy;
+    h->flags = flags;
+    h->cap = cap;
+    h->lock = 0;
+    h->err = 0;
+    h->n_ext = budget > 0 ? 1 : 0;
+    h->q_len = 0;
+    h->ring_tail = 0;
+    h->n_done = 0;
+    E.ext_off[0] = 0;
+    E.ext_len[0] = budget;
+  }
+}
+
+// Declare tickets [first, first + count): their needs come from `jobs`
+// (ticket i = job i) or, for a single ticket, from (need, prio).
+__global__ void k_declare(Eng E, uint32_t first, uint32_t count, const sg_job* jobs, uint64_t need,
+                          int32_t prio, uint32_t exclusive) {
+  if (threadIdx.x >= 32) return;
+  for (uint32_t t = first; t < first + count; t++) {
+    if (!eng_lock(E)) return;
+    Sess s = sess_load(E);
+    uint64_t raw = jobs ? jobs[t].need : need;
+    int32_t pr = jobs ? (int32_t)jobs[t].prio : prio;
+    uint64_t g = exclusive ? s.budget : round_need(raw, s.granule);
+    if (lane_id() == 0) {
+      stcg(E.need_g + t, g);
+      stcg(E.need_raw + t, exclusive ? s.budget : raw);
+      stcg(E.prio + t, pr);
+      stcg(E.blk_done + t, 0u);
+    }
+    __syncwarp();
+    op_declare(E, s, t, globaltimer_ns(), -1, nullptr, nullptr, nullptr);
+    sess_store(E, s);
+    eng_unlock(E);
+  }
+}
+
+__global__ void k_release(Eng E, uint32_t t, uint64_t bytes) {
+  if (threadIdx.x >= 32) return;
+  eng_release_locked(E, t, bytes);
+}
+
+__global__ void k_cancel(Eng E, uint32_t t) {
+  if (threadIdx.x >= 32) return;
+  if (!eng_lock(E)) return;
+  Sess s = sess_load(E);
+  op_cancel(E, s, t, globaltimer_ns(), nullptr, nullptr);
+  sess_store(E, s);
+  eng_unlock(E);
+}
+
+// Replay: the whole event loop of a trace on one warp, logical clock.
+// Events at equal time: completions, then arrivals, then timeouts, then by
+// ticket id (the same total order as the oracle).
+__global__ void k_replay(Eng E, const sg_job* __restrict__ jobs, uint32_t n, uint32_t exclusive,
+                         uint64_t* dur, uint64_t* tmo, EvHeap H, uint64_t* stats) {
+  if (threadIdx.x >= 32) return;
+  const uint32_t lane = lane_id();
+  const EngHdr* h0 = E.hdr;
+  const uint64_t budget = h0->budget, granule = h0->granule;
+  uint32_t bad = 0;
+  for (uint32_t j = lane; j < n; j += 32) {
+    const sg_job& jb = jobs[j];
+    uint64_t g = exclusive ? budget : round_need(jb.need, granule);
+    E.need_g[j] = g;
+    E.need_raw[j] = exclusive ? budget : jb.need;
+    E.prio[j] = jb.prio;
+    E.status[j] = ST_PENDING;
+    dur[j] = jb.duration_ns;
+    tmo[j] = jb.timeout_ns;
+    sg_record r;
+    r.status = ST_PENDING; r.slot = -1; r.grant_seq = -1; r.grant_t = 0; r.offset = 0;
+    r.done_t = 0; r.arrival_t = jb.arrival_ns;
+    E.rec[j] = r;
+    if (j > 0 && jobs[j - 1].arrival_ns > jb.arrival_ns) bad = 1;
+  }
+  __syncwarp();
+  Sess s = sess_load(E);
+  if (__any_sync(SG_FULL, bad)) s.err |= ERR_ORDER;
+  uint32_t na = 0;
+  while (s.err == 0) {
+    bool has_a = na < n;
+    bool has_e = H.n > 0;
+    if (!has_a && !has_e) break;
+    uint64_t et = 0, ek = 0, at = 0, ak = 0;
+    if (has_e) { et = H.t[0]; ek = H.k[0]; }
+    if (has_a) { at = jobs[na].arrival_ns; ak = ((uint64_t)EV_ARRIVE << 32) | na; }
+    bool take_e = has_e && (!has_a || ev_less(et, ek, at, ak));
+    if (take_e) {
+      heap_pop(H);
+      uint32_t type = (uint32_t)(ek >> 32), j = (uint32_t)ek;
+      if (type == EV_COMPLETE) op_release(E, s, j, 0, et, &H, dur);
+      else op_cancel(E, s, j, et, &H, dur);
+    } else {
+      op_declare(E, s, na, at, -1, &H, dur, tmo);
+      na++;
+    }
+  }
+  sess_store(E, s);
+  if (stats && lane == 0) {
+    stats[0] = s.peak;
+    stats[1] = s.frag;
+    stats[2] = s.passes;
+    stats[3] = s.err | ldcg(&E.hdr->err);
+  }
+}
+
+// ------------------------------------------------------- device layout
+struct DevLayout {
+  uint64_t hdr, need_g, need_raw, prio, status, blk_done, q, ext_off, ext_len, rec, extra, total;
+};
+
+DevLayout dev_layout(uint32_t cap, bool with_rec, uint64_t extra_bytes) {
+  auto a256 = [](uint64_t x) { return (x + 255) / 256 * 256; };
+  DevLayout L;
+  uint64_t o = 0;
+  L.hdr = o; o += a256(sizeof(EngHdr));
+  L.need_g = o; o += a256(8ull * cap);
+  L.need_raw = o; o += a256(8ull * cap);
+  L.prio = o; o += a256(4ull * cap);
+  L.status = o; o += a256(4ull * cap);
+  L.blk_done = o; o += a256(4ull * cap);
+  L.q = o; o += a256(4ull * (cap + 1));
+  L.ext_off = o; o += a256(8ull * (cap + 2));
+  L.ext_len = o; o += a256(8ull * (cap + 2));
+  L.rec = o; if (with_rec) o += a256(sizeof(sg_record) * (uint64_t)cap);
+  L.extra = o; o += a256(extra_bytes);
+  L.total = o;
+  return L;
+}
+
+Eng eng_from(char* base, const DevLayout& L) {
+  Eng E;
+  memset(&E, 0, sizeof E);
+  E.hdr = (EngHdr*)(base + L.hdr);
+  E.need_g = (uint64_t*)(base + L.need_g);
+  E.need_raw = (uint64_t*)(base + L.need_raw);
+  E.prio = (int32_t*)(base + L.prio);
+  E.status = (uint32_t*)(base + L.status);
+  E.blk_done = (uint32_t*)(base + L.blk_done);
+  E.q = (uint32_t*)(base + L.q);
+  E.ext_off = (uint64_t*)(base + L.ext_off);
+  E.ext_len = (uint64_t*)(base + L.ext_len);
+  E.rec = (sg_record*)(base + L.rec);
+  return E;
+}
+
+uint64_t now_ns() {
+  return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+inline void cpu_relax() {
+#if defined(__x86_64__)
+  __builtin_ia32_pause();
+#endif
+}
+
+uint64_t nearest_rank(std::vector<uint64_t>& v, double p) {
+  if (v.empty()) return 0;
+  std::sort(v.begin(), v.end());
+  double r = p * (double)v.size();
+  uint64_t k = (uint64_t)r;
+  if ((double)k < r) k++;
+  if (k < 1) k = 1;
+  return v[k - 1];
+}
+
+}  // namespace
+
+// ================================================================ context
+struct sg_ctx {
+  int device = 0;
+  char* pool = nullptr;
+  uint64_t pool_bytes = 0, budget = 0, granule = 256;
+  uint32_t policy = 0, flags = 0, cap = 0, n_slots = 0;
+  char* dev = nullptr;           // engine state
+  DevLayout L{};
+  Eng eng{};
+  char* mapped = nullptr;        // host-mapped publication block
+  volatile sg_record* h_rec = nullptr;
+  volatile uint32_t* h_ring = nullptr;
+  volatile uint32_t* h_hdr = nullptr;
+  sg_job* d_jobs = nullptr;      // [cap] job records for sg_run_trace
+  uint64_t* d_keep = nullptr;    // [cap] output digests
+  uint32_t* d_err = nullptr;     // generator error flags
+  std::mutex mu;
+  uint32_t next_ticket = 0;
+  std::vector<uint8_t> rel_enq;  // a full release is already enqueued
+  cudaStream_t ctrl = nullptr;
+  std::vector<cudaStream_t> slots;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<cudaEvent_t> slot_ev;
+};
+
+#define CK(x)                                 \
+  do {                                        \
+    if ((x) != cudaSuccess) return SG_ERR_CUDA; \
+  } while (0)
+
+static void ctx_free(sg_ctx* c) {
+  if (!c) return;
+  for (auto s : c->slots) if (s) cudaStreamDestroy(s);
+  for (auto e : c->slot_ev) if (e) cudaEventDestroy(e);
+  if (c->ctrl) cudaStreamDestroy(c->ctrl);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->dev) cudaFree(c->dev);
+  if (c->mapped) cudaFreeHost(c->mapped);
+  delete c;
+}
+
+static int ctx_reset_locked(sg_ctx* c) {
+  for (auto s : c->slots) CK(cudaStreamSynchronize(s));
+  CK(cudaStreamSynchronize(c->ctrl));
+  k_eng_reset<<<64, 256, 0, c->ctrl>>>(c->eng, c->budget, c->granule, c->policy, c->flags, c->cap);
+  CK(cudaGetLastError());
+  CK(cudaMemsetAsync(c->d_err, 0, 4, c->ctrl));
+  CK(cudaStreamSynchronize(c->ctrl));
+  for (uint32_t i = 0; i < c->cap; i++) {
+    c->h_rec[i].status = SG_ST_PENDING;
+    c->h_rec[i].grant_seq = -1;
+  }
+  c->h_hdr[0] = 0;
+  c->h_hdr[1] = 0;
+  c->h_hdr[2] = 0;
+  c->next_ticket = 0;
+  std::fill(c->rel_enq.begin(), c->rel_enq.end(), 0);
+  return SG_OK;
+}
+
+extern "C" int sg_init(sg_ctx** out, void* dev_pool, uint64_t pool_bytes, const sg_config* cfg) {
+  if (!out) return SG_ERR_INVALID;
+  *out = nullptr;
+  sg_config d{};
+  if (cfg) d = *cfg;
+  if (d.policy > SG_POLICY_PRIO_FIRST_FIT) return SG_ERR_INVALID;
+  uint64_t granule = d.granule ? d.granule : 256;
+  if (granule < 256 || (granule & (granule - 1))) return SG_ERR_INVALID;
+  if (!dev_pool || ((uintptr_t)dev_pool % 256) || pool_bytes < granule) return SG_ERR_INVALID;
+  uint32_t cap = d.max_tickets ? d.max_tickets : (1u << 17);
+  if (cap > (1u << 24)) return SG_ERR_INVALID;
+  sg_ctx* c = new sg_ctx();
+  c->pool = (char*)dev_pool;
+  c->pool_bytes = pool_bytes;
+  c->granule = granule;
+  c->budget = pool_bytes / granule * granule;
+  c->policy = d.policy;
+  c->flags = d.flags;
+  c->cap = cap;
+  c->n_slots = d.n_streams ? d.n_streams : 48;
+  c->rel_enq.assign(cap, 0);
+  int rc = SG_ERR_CUDA;
+  do {
+    if (cudaGetDevice(&c->device) != cudaSuccess) break;
+    uint64_t extra = 64ull * cap + 8ull * cap + 256;  // jobs, keep, err
+    c->L = dev_layout(cap, true, extra);
+    if (cudaMalloc(&c->dev, c->L.total) != cudaSuccess) break;
+    c->eng = eng_from(c->dev, c->L);
+    c->d_jobs = (sg_job*)(c->dev + c->L.extra);
+    c->d_keep = (uint64_t*)(c->dev + c->L.extra + 64ull * cap);
+    c->d_err = (uint32_t*)(c->dev + c->L.extra + 72ull * cap);
+    uint64_t mbytes = sizeof(sg_record) * (uint64_t)cap + 4ull * cap + 256;
+    if (cudaHostAlloc((void**)&c->mapped, mbytes, cudaHostAllocMapped | cudaHostAllocPortable) !=
+        cudaSuccess)
+      break;
+    memset(c->mapped, 0, mbytes);
+    c->h_rec = (volatile sg_record*)c->mapped;
+    c->h_ring = (volatile uint32_t*)(c->mapped + sizeof(sg_record) * (uint64_t)cap);
+    c->h_hdr = (volatile uint32_t*)(c->mapped + sizeof(sg_record) * (uint64_t)cap + 4ull * cap);
+    void* dp = nullptr;
+    if (cudaHostGetDevicePointer(&dp, c->mapped, 0) != cudaSuccess) break;
+    char* dm = (char*)dp;
+    c->eng.pub_rec = (sg_record*)dm;
+    c->eng.pub_ring = (uint32_t*)(dm + sizeof(sg_record) * (uint64_t)cap);
+    c->eng.pub_hdr = (uint32_t*)(dm + sizeof(sg_record) * (uint64_t)cap + 4ull * cap);
+    int lo = 0, hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) break;
+    if (cudaStreamCreateWithPriority(&c->ctrl, cudaStreamNonBlocking, hi) != cudaSuccess) break;
+    c->slots.assign(c->n_slots, nullptr);
+    c->slot_ev.assign(c->n_slots, nullptr);
+    bool ok = true;
+    for (uint32_t i = 0; i < c->n_slots && ok; i++) {
+      ok = cudaStreamCreateWithPriority(&c->slots[i], cudaStreamNonBlocking, lo) == cudaSuccess &&
+           cudaEventCreateWithFlags(&c->slot_ev[i], cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) break;
+    if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) break;
+    rc = ctx_reset_locked(c);
+  } while (0);
+  if (rc != SG_OK) {
+    ctx_free(c);
+    return rc;
+  }
+  *out = c;
+  return SG_OK;
+}
+
+extern "C" int sg_reset(sg_ctx* c) {
+  if (!c) return SG_ERR_INVALID;
+  std::lock_guard<std::mutex> g(c->mu);
+  return ctx_reset_locked(c);
+}
+
+extern "C" uint32_t sg_device_error(sg_ctx* c) { return c ? c->h_hdr[1] : 0u; }
+
+extern "C" int sg_declare(sg_ctx* c, uint64_t need, int32_t priority, sg_ticket* out) {
+  if (!c || !out) return SG_ERR_INVALID;
+  uint64_t g = (need + c->granule - 1) / c->granule * c->granule;
+  if (g > c->budget) return SG_ERR_TOO_LARGE;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (c->next_ticket >= c->cap) return SG_ERR_CAPACITY;
+  uint32_t t = c->next_ticket++;
+  c->h_rec[t].status = SG_ST_PENDING;
+  k_declare<<<1, 32, 0, c->ctrl>>>(c->eng, t, 1, nullptr, need, priority, 0);
+  if (cudaGetLastError() != cudaSuccess) return SG_ERR_CUDA;
+  *out = t;
+  return SG_OK;
+}
+
+static int grant_of(sg_ctx* c, sg_ticket t, sg_grant* out) {
+  uint32_t st = (uint32_t)c->h_rec[t].status;
+  if (st == SG_ST_RUNNING) {
+    if (out) {
+      out->offset = c->h_rec[t].offset;
+      out->ptr = c->pool + out->offset;
+      out->grant_time_ns = c->h_rec[t].grant_t;
+    }
+    return SG_OK;
+  }
+  if (st == SG_ST_PENDING || st == SG_ST_QUEUED) return SG_NOT_READY;
+  if (st == SG_ST_TIMEOUT) return SG_ERR_TIMEOUT;
+  return SG_ERR_INVALID;
+}
+
+extern "C" int sg_try(sg_ctx* c, sg_ticket t, sg_grant* out) {
+  if (!c || t >= c->cap) return SG_ERR_INVALID;
+  if (c->h_hdr[1]) return SG_ERR_DEVICE;
+  return grant_of(c, t, out);
+}
+
+extern "C" int sg_wait(sg_ctx* c, sg_ticket t, uint64_t timeout_ns, sg_grant* out) {
+  if (!c || t >= c->cap) return SG_ERR_INVALID;
+  uint64_t t0 = now_ns();
+  for (;;) {
+    int rc = grant_of(c, t, out);
+    if (rc != SG_NOT_READY) return rc;
+    if (c->h_hdr[1]) return SG_ERR_DEVICE;
+    if (now_ns() - t0 >= timeout_ns) break;
+    for (int i = 0; i < 64; i++) cpu_relax();
+  }
+  // expired: withdraw the request (re-runs the notification pass)
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    k_cancel<<<1, 32, 0, c->ctrl>>>(c->eng, t);
+    if (cudaGetLastError() != cudaSuccess) return SG_ERR_CUDA;
+    if (cudaStreamSynchronize(c->ctrl) != cudaSuccess) return SG_ERR_CUDA;
+  }
+  int rc = grant_of(c, t, out);
+  return rc == SG_NOT_READY ? SG_ERR_DEVICE : rc;
+}
+
+extern "C" int sg_release(sg_ctx* c, sg_ticket t, uint64_t bytes, void* stream) {
+  if (!c || t >= c->cap) return SG_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if ((uint32_t)c->h_rec[t].status != SG_ST_RUNNING || c->rel_enq[t]) return SG_ERR_INVALID;
+  if (bytes == 0) c->rel_enq[t] = 1;
+  k_release<<<1, 32, 0, (cudaStream_t)stream>>>(c->eng, t, bytes);
+  return cudaGetLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
+}
+
+extern "C" int sg_launch(sg_ctx* c, sg_ticket t, const sg_job* job, const uint64_t* tables_dev,
+                         void* stream) {
+  if (!c || !job || t >= c->cap) return SG_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if ((uint32_t)c->h_rec[t].status != SG_ST_RUNNING || c->rel_enq[t]) return SG_ERR_INVALID;
+  RelHook h;
+  h.eng = c->eng;
+  h.ticket = t;
+  h.active = 1;
+  char* base = c->pool + c->h_rec[t].offset;
+  int rc = launch_job(*job, base, tables_dev, h, nullptr, c->d_err, (cudaStream_t)stream, nullptr);
+  if (rc == SG_OK) c->rel_enq[t] = 1;
+  return rc;
+}
+
+extern "C" int sg_shutdown(sg_ctx* c) {
+  if (!c) return SG_ERR_INVALID;
+  int rc = SG_OK;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    for (auto s : c->slots) if (cudaStreamSynchronize(s) != cudaSuccess) rc = SG_ERR_CUDA;
+    if (cudaStreamSynchronize(c->ctrl) != cudaSuccess) rc = SG_ERR_CUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) rc = SG_ERR_CUDA;
+    for (uint32_t t = 0; t < c->next_ticket && rc == SG_OK; t++) {
+      uint32_t st = (uint32_t)c->h_rec[t].status;
+      if (st == SG_ST_RUNNING && !c->rel_enq[t]) k_release<<<1, 32, 0, c->ctrl>>>(c->eng, t, 0);
+      else if (st == SG_ST_QUEUED || st == SG_ST_PENDING) k_cancel<<<1, 32, 0, c->ctrl>>>(c->eng, t);
+    }
+    if (cudaStreamSynchronize(c->ctrl) != cudaSuccess) rc = SG_ERR_CUDA;
+  }
+  ctx_free(c);
+  return rc;
+}
+
+// ================================================================ runner
+extern "C" int sg_run_trace(sg_ctx* c, const sg_job* jobs, uint32_t n, const uint64_t* tables_dev,
+                            uint32_t mode, sg_record* log, uint64_t* keep, sg_run_stats* stats) {
+  if (!c || (!jobs && n)) return SG_ERR_INVALID;
+  if (n > c->cap) return SG_ERR_CAPACITY;
+  std::lock_guard<std::mutex> lk(c->mu);
+  const bool host_io = mode & SG_RUN_HOST_IO;
+  const bool timed = (mode & SG_RUN_TIMED) && !(mode & SG_RUN_SATURATED);
+  const bool excl = mode & SG_RUN_EXCLUSIVE;
+  const bool want_keep = (mode & SG_RUN_KEEP) && keep;
+  int rc = ctx_reset_locked(c);
+  if (rc != SG_OK) return rc;
+  std::vector<sg_job> hj(n);
+  if (n) {
+    if (host_io) {
+      memcpy(hj.data(), jobs, sizeof(sg_job) * n);
+      CK(cudaMemcpyAsync(c->d_jobs, jobs, sizeof(sg_job) * n, cudaMemcpyHostToDevice, c->ctrl));
+    } else {
+      CK(cudaMemcpyAsync(c->d_jobs, jobs, sizeof(sg_job) * n, cudaMemcpyDeviceToDevice, c->ctrl));
+      CK(cudaMemcpyAsync(hj.data(), jobs, sizeof(sg_job) * n, cudaMemcpyDeviceToHost, c->ctrl));
+    }
+    if (want_keep) CK(cudaMemsetAsync(c->d_keep, 0, 8ull * n, c->ctrl));
+  }
+  CK(cudaStreamSynchronize(c->ctrl));
+  uint64_t launches = 0;
+  std::vector<int32_t> slot_ticket(c->n_slots, -1);
+  std::vector<uint8_t> slot_used(c->n_slots, 0);
+  std::vector<uint32_t> pending;
+  pending.reserve(n);
+  uint32_t ring_head = 0, failed = 0;
+  CK(cudaEventRecord(c->ev0, c->ctrl));
+  uint32_t declared = 0;
+  const uint64_t t0 = now_ns();
+  if (!timed && n) {
+    k_declare<<<1, 32, 0, c->ctrl>>>(c->eng, 0, n, c->d_jobs, 0, 0, excl ? 1u : 0u);
+    CK(cudaGetLastError());
+    launches++;
+    declared = n;
+  }
+  uint64_t last_progress = now_ns();
+  uint32_t last_done = 0;
+  size_t pend_pos = 0;
+  uint32_t rr = 0;
+  while (true) {
+    if (timed && declared < n) {
+      uint64_t el = now_ns() - t0;
+      uint32_t k = declared;
+      while (k < n && hj[k].arrival_ns <= el) k++;
+      if (k > declared) {
+        k_declare<<<1, 32, 0, c->ctrl>>>(c->eng, declared, k - declared, c->d_jobs, 0, 0, excl ? 1u : 0u);
+        CK(cudaGetLastError());
+        launches++;
+        declared = k;
+      }
+    }
+    uint32_t tail = c->h_hdr[0];
+    while (ring_head < tail) pending.push_back((uint32_t)c->h_ring[(ring_head++) % c->cap]);
+    while (pend_pos < pending.size()) {
+      // a slot whose last job has released its memory (or was never used)
+      int slot = -1;
+      for (uint32_t k = 0; k < c->n_slots; k++) {
+        uint32_t s = (rr + k) % c->n_slots;
+        int32_t tk = slot_ticket[s];
+        if (tk < 0 || (uint32_t)c->h_rec[tk].status >= SG_ST_DONE) { slot = (int)s; break; }
+      }
+      if (slot < 0) break;
+      rr = (uint32_t)slot + 1;
+      uint32_t t = pending[pend_pos++];
+      RelHook h;
+      h.eng = c->eng;
+      h.ticket = t;
+      h.active = 1;
+      char* base = c->pool + c->h_rec[t].offset;
+      int lrc = launch_job(hj[t], base, tables_dev, h, want_keep ? c->d_keep + t : nullptr, c->d_err,
+                           c->slots[slot], &launches);
+      if (lrc != SG_OK) {
+        // the job cannot run: give its memory back so no waiter is lost
+        cudaGetLastError();
+        k_release<<<1, 32, 0, c->slots[slot]>>>(c->eng, t, 0);
+        launches++;
+        failed++;
+      }
+      c->rel_enq[t] = 1;
+      slot_ticket[slot] = (int32_t)t;
+      slot_used[slot] = 1;
+    }
+    uint32_t done = c->h_hdr[2];
+    if (done >= n && declared >= n) break;
+    if (c->h_hdr[1]) break;
+    uint64_t tn = now_ns();
+    if (done != last_done || ring_head != pend_pos) {
+      last_done = done;
+      last_progress = tn;
+    } else if (tn - last_progress > 120ull * 1000000000ull) {
+      break;  // no progress for two minutes: stop waiting, report below
+    }
+    for (int i = 0; i < 16; i++) cpu_relax();
+  }
+  for (uint32_t s = 0; s < c->n_slots; s++) {
+    if (!slot_used[s]) continue;
+    CK(cudaEventRecord(c->slot_ev[s], c->slots[s]));
+    CK(cudaStreamWaitEvent(c->ctrl, c->slot_ev[s], 0));
+  }
+  CK(cudaEventRecord(c->ev1, c->ctrl));
+  CK(cudaStreamSynchronize(c->ctrl));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  uint32_t err = c->h_hdr[1];
+  uint32_t derr = 0;
+  CK(cudaMemcpy(&derr, c->d_err, 4, cudaMemcpyDeviceToHost));
+  if (log && n) {
+    CK(cudaMemcpyAsync(log, c->eng.rec, sizeof(sg_record) * n,
+                       host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->ctrl));
+  }
+  if (want_keep && n) {
+    CK(cudaMemcpyAsync(keep, c->d_keep, 8ull * n,
+                       host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->ctrl));
+  }
+  CK(cudaStreamSynchronize(c->ctrl));
+  uint32_t n_done = 0, n_bad = 0;
+  uint64_t first = ~0ull, last = 0;
+  std::vector<uint64_t> waits, turns;
+  waits.reserve(n);
+  turns.reserve(n);
+  for (uint32_t j = 0; j < n; j++) {
+    uint32_t st = (uint32_t)c->h_rec[j].status;
+    if (st != SG_ST_DONE) { n_bad++; continue; }
+    n_done++;
+    uint64_t a = c->h_rec[j].arrival_t, g = c->h_rec[j].grant_t, d = c->h_rec[j].done_t;
+    first = std::min(first, a);
+    last = std::max(last, d);
+    waits.push_back(g - a);
+    turns.push_back(d - a);
+  }
+  if (stats) {
+    memset(stats, 0, sizeof *stats);
+    stats->elapsed_ns = (uint64_t)((double)ms * 1e6);
+    stats->makespan_ns = n_done ? last - first : 0;
+    stats->wait_p50_ns = nearest_rank(waits, 0.50);
+    stats->wait_p99_ns = nearest_rank(waits, 0.99);
+    stats->turnaround_p50_ns = nearest_rank(turns, 0.50);
+    stats->turnaround_p99_ns = nearest_rank(turns, 0.99);
+    EngHdr hh;
+    CK(cudaMemcpy(&hh, c->eng.hdr, sizeof hh, cudaMemcpyDeviceToHost));
+    stats->peak_used = hh.peak_used;
+    stats->frag_waits = hh.frag_waits;
+    stats->passes = hh.passes;
+    stats->launches = launches;
+    stats->jobs_done = n_done;
+    stats->jobs_failed = n_bad + failed;
+  }
+  if (err || derr) return SG_ERR_DEVICE;
+  if (n_done + failed < n && n_bad > 0) return failed ? SG_ERR_INVALID : SG_ERR_DEVICE;
+  return failed ? SG_ERR_INVALID : SG_OK;
+}
+
+// ================================================================ replay
+extern "C" uint64_t sg_replay_workspace_bytes(uint32_t n) {
+  uint64_t cap = n ? n : 1;
+  uint64_t extra = 16ull * cap + 16ull * (2 * cap + 1);   // dur, tmo, heap t/k
+  return dev_layout((uint32_t)cap, false, extra).total;
+}
+
+extern "C" int sg_replay(const sg_job* jobs_dev, uint32_t n, uint64_t budget, uint64_t granule,
+                         uint32_t policy, uint32_t flags, uint32_t exclusive, sg_record* log_dev,
+                         void* workspace_dev, uint64_t* stats_dev, void* stream) {
+  if (n == 0) return SG_OK;
+  if (!jobs_dev || !log_dev || !workspace_dev || policy > SG_POLICY_PRIO_FIRST_FIT) return SG_ERR_INVALID;
+  if (granule == 0) granule = 256;
+  if (granule & (granule - 1)) return SG_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t cap = n;
+  uint64_t extra = 16ull * cap + 16ull * (2ull * cap + 1);
+  DevLayout L = dev_layout(cap, false, extra);
+  char* base = (char*)workspace_dev;
+  Eng E = eng_from(base, L);
+  E.rec = log_dev;
+  uint64_t* dur = (uint64_t*)(base + L.extra);
+  uint64_t* tmo = dur + cap;
+  EvHeap H;
+  H.t = tmo + cap;
+  H.k = H.t + (2ull * cap + 1);
+  H.n = 0;
+  H.cap = 2 * cap + 1;
+  uint64_t b = budget / granule * granule;
+  k_eng_reset<<<8, 256, 0, st>>>(E, b, granule, policy, flags, cap);
+  k_replay<<<1, 32, 0, st>>>(E, jobs_dev, n, exclusive, dur, tmo, H, stats_dev);
+  return cudaGetLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
+}
+
+extern "C" const char* sg_strerror(int code) {
+  switch (code) {
+    case SG_OK: return "ok";
+    case SG_NOT_READY: return "not ready: request queued";
+    case SG_ERR_TIMEOUT: return "timeout: request withdrawn";
+    case SG_ERR_TOO_LARGE: return "need exceeds the pool";
+    case SG_ERR_INVALID: return "invalid argument or ticket state";
+    case SG_ERR_CUDA: return "CUDA error";
+    case SG_ERR_UNKNOWN: return "unknown error";
+    case SG_ERR_CAPACITY: return "ticket table full";
+    case SG_ERR_DEVICE: return "device engine error";
+    default: return "unrecognised code";
+  }
+}

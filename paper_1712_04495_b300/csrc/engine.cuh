@@ -1,0 +1,585 @@
+// Device-resident admission and notification engine (arXiv 1712.04495).
+//
+// The shared state of Sec. III-B -- total memory, total used, per-client
+// grants and the queue of waiting clients -- lives in device memory. One
+// warp at a time owns it (a device spin lock with a bounded wait) and runs
+// the life-cycle operations of Sec. IV on it:
+//   declare  = pre-allocation: queue the request, run the admission pass;
+//   release  = post-free: free the extent, run the notification pass;
+//   cancel   = a blocking pre-allocation whose timeout expired.
+// The notification passes are the four policies of Sec. V.
+//
+// Every operation is executed by all 32 lanes of a warp in lock step: scalar
+// state sits in lane-uniform registers, and array scans and shifts are
+// spread over the lanes (ballot for "first index that ...", chunked copies
+// for shifts). The result equals the sequential definition step for step,
+// which is what makes replay logs bit-exact against the CPU oracle.
+//
+// Placement: the pool is a list of free extents sorted by offset and kept
+// coalesced; a request (rounded up to the granule) goes to the lowest
+// address extent that holds it. A request is served only if it fits the
+// byte count (budget - used) and can be placed.
+#pragma once
+#include "common.cuh"
+
+namespace sg {
+
+enum : uint32_t { ST_PENDING = 0, ST_QUEUED = 1, ST_RUNNING = 2, ST_DONE = 3, ST_TIMEOUT = 4,
+                  ST_TOO_LARGE = 5 };
+enum : uint32_t { ERR_LOCK = 1u, ERR_STATE = 2u, ERR_ORDER = 4u, ERR_HEAP = 8u, ERR_NNZ = 16u,
+                  ERR_CAP = 32u };
+
+struct EngHdr {            // scalar state, device memory
+  uint64_t budget, granule, used, seq, peak_used, frag_waits, passes;
+  uint32_t policy, flags, cap, lock, err, n_ext, q_len, ring_tail, n_done, pad;
+};
+
+struct Eng {               // array pointers (kernel parameter, by value)
+  EngHdr* hdr;
+  uint64_t* need_g;        // [cap] granule-rounded held / requested bytes
+  uint64_t* need_raw;      // [cap] declared bytes
+  int32_t* prio;           // [cap]
+  uint32_t* status;        // [cap]
+  uint32_t* blk_done;      // [cap] finished blocks of a ticket's final kernel
+  uint32_t* q;             // [cap] waiting tickets in service order
+  uint64_t* ext_off;       // [cap + 2] free extents, sorted, coalesced
+  uint64_t* ext_len;       // [cap + 2]
+  sg_record* rec;          // [cap] per-ticket log (device)
+  sg_record* pub_rec;      // [cap] host-mapped copy of the log, or null
+  uint32_t* pub_ring;      // [cap] host-mapped ring of granted tickets, or null
+  uint32_t* pub_hdr;       // host-mapped: [0] ring tail, [1] error flags, [2] done count
+};
+
+// Lane-uniform register copy of the scalar state for one locked session.
+struct Sess {
+  uint64_t budget, granule, used, seq, peak, frag, passes;
+  uint32_t policy, flags, cap, n_ext, q_len, ring_tail, n_done, err;
+};
+
+// Replay only: min-heap of pending completion / timeout events.
+struct EvHeap {
+  uint64_t* t;             // [cap] event time
+  uint64_t* k;             // [cap] (type << 32) | ticket
+  uint32_t n, cap;
+};
+
+__device__ __forceinline__ Sess sess_load(const Eng& E) {
+  Sess s;
+  const EngHdr* h = E.hdr;
+  s.budget = ldcg(&h->budget);
+  s.granule = ldcg(&h->granule);
+  s.used = ldcg(&h->used);
+  s.seq = ldcg(&h->seq);
+  s.peak = ldcg(&h->peak_used);
+  s.frag = ldcg(&h->frag_waits);
+  s.passes = ldcg(&h->passes);
+  s.policy = ldcg(&h->policy);
+  s.flags = ldcg(&h->flags);
+  s.cap = ldcg(&h->cap);
+  s.n_ext = ldcg(&h->n_ext);
+  s.q_len = ldcg(&h->q_len);
+  s.ring_tail = ldcg(&h->ring_tail);
+  s.n_done = ldcg(&h->n_done);
+  s.err = 0;
+  return s;
+}
+
+__device__ __forceinline__ void sess_store(const Eng& E, const Sess& s) {
+  __syncwarp();
+  if (lane_id() == 0) {
+    EngHdr* h = E.hdr;
+    stcg(&h->used, s.used);
+    stcg(&h->seq, s.seq);
+    stcg(&h->peak_used, s.peak);
+    stcg(&h->frag_waits, s.frag);
+    stcg(&h->passes, s.passes);
+    stcg(&h->n_ext, s.n_ext);
+    stcg(&h->q_len, s.q_len);
+    stcg(&h->ring_tail, s.ring_tail);
+    stcg(&h->n_done, s.n_done);
+    if (s.err) {
+      atomicOr(&h->err, s.err);
+      if (E.pub_hdr) atomicOr_system(&E.pub_hdr[1], s.err);
+    }
+  }
+  __syncwarp();
+}
+
+// ------------------------------------------------------------------ lock
+// Spin on the engine lock with a bounded wait (globaltimer); on expiry the
+// caller gets false and the error flag is raised. Warp-uniform result.
+__device__ __forceinline__ bool eng_lock(const Eng& E, uint64_t limit_ns = 2000000000ull) {
+  int ok = 0;
+  if (lane_id() == 0) {
+    uint64_t t0 = globaltimer_ns();
+    unsigned ns = 32;
+    for (;;) {
+      if (atomicCAS(&E.hdr->lock, 0u, 1u) == 0u) { ok = 1; break; }
+      if (globaltimer_ns() - t0 > limit_ns) break;
+      __nanosleep(ns);
+      if (ns < 1024) ns <<= 1;
+    }
+    if (!ok) {
+      atomicOr(&E.hdr->err, ERR_LOCK);
+      if (E.pub_hdr) atomicOr_system(&E.pub_hdr[1], ERR_LOCK);
+    }
+    __threadfence();
+  }
+  ok = __shfl_sync(SG_FULL, ok, 0);
+  return ok != 0;
+}
+
+__device__ __forceinline__ void eng_unlock(const Eng& E) {
+  __syncwarp();
+  if (lane_id() == 0) {
+    __threadfence();
+    atomicExch(&E.hdr->lock, 0u);
+  }
+  __syncwarp();
+}
+
+// -------------------------------------------------------- warp primitives
+// first index i in [from, len) with pred(i), or -1 (warp-uniform)
+template <typename Pred>
+__device__ __forceinline__ int64_t warp_find_first(uint32_t from, uint32_t len, Pred pred) {
+  for (uint32_t base = from; base < len; base += 32) {
+    uint32_t i = base + lane_id();
+    bool p = (i < len) && pred(i);
+    unsigned m = __ballot_sync(SG_FULL, p);
+    if (m) return (int64_t)base + (__ffs(m) - 1);
+  }
+  return -1;
+}
+
+// remove element at index i from an array of length len (shift left)
+template <typename T>
+__device__ __forceinline__ void warp_remove_at(T* a, uint32_t i, uint32_t len) {
+  for (uint32_t base = i; base + 1 < len; base += 32) {
+    uint32_t k = base + lane_id();
+    T v{};
+    bool act = k + 1 < len;
+    if (act) v = ldcg(a + k + 1);
+    __syncwarp();
+    if (act) stcg(a + k, v);
+    __syncwarp();
+  }
+}
+
+// insert v at index i of an array of length len (shift right)
+template <typename T>
+__device__ __forceinline__ void warp_insert_at(T* a, uint32_t i, uint32_t len, T v) {
+  // move a[i .. len-1] to a[i+1 .. len], top chunk first
+  for (int64_t top = (int64_t)len; top > (int64_t)i; top -= 32) {
+    int64_t k = top - (int64_t)lane_id();   // destination index
+    bool act = k > (int64_t)i;
+    T x{};
+    if (act) x = ldcg(a + k - 1);
+    __syncwarp();
+    if (act) stcg(a + k, x);
+    __syncwarp();
+  }
+  if (lane_id() == 0) stcg(a + i, v);
+  __syncwarp();
+}
+
+// --------------------------------------------------------------- extents
+__device__ __forceinline__ int64_t ext_find(const Eng& E, const Sess& s, uint64_t g) {
+  const uint64_t* len = E.ext_len;
+  return warp_find_first(0, s.n_ext, [&](uint32_t i) { return ldcg(len + i) >= g; });
+}
+
+// take g bytes from the front of extent e
+__device__ __forceinline__ uint64_t ext_take(const Eng& E, Sess& s, uint32_t e, uint64_t g) {
+  uint64_t off = ldcg(E.ext_off + e);
+  uint64_t len = ldcg(E.ext_len + e);
+  __syncwarp();
+  if (len == g) {
+    warp_remove_at(E.ext_off, e, s.n_ext);
+    warp_remove_at(E.ext_len, e, s.n_ext);
+    s.n_ext -= 1;
+  } else {
+    if (lane_id() == 0) {
+      stcg(E.ext_off + e, off + g);
+      stcg(E.ext_len + e, len - g);
+    }
+    __syncwarp();
+  }
+  return off;
+}
+
+// return [off, off+g) to the free list, merging with neighbours
+__device__ __forceinline__ void ext_give(const Eng& E, Sess& s, uint64_t off, uint64_t g) {
+  const uint64_t* eo = E.ext_off;
+  int64_t p = warp_find_first(0, s.n_ext, [&](uint32_t i) { return ldcg(eo + i) > off; });
+  uint32_t ip = p < 0 ? s.n_ext : (uint32_t)p;
+  bool left = false, right = false;
+  uint64_t ll = 0, rl = 0;
+  if (ip > 0) {
+    uint64_t lo = ldcg(E.ext_off + ip - 1);
+    ll = ldcg(E.ext_len + ip - 1);
+    left = lo + ll == off;
+  }
+  if (ip < s.n_ext) {
+    uint64_t ro = ldcg(E.ext_off + ip);
+    rl = ldcg(E.ext_len + ip);
+    right = off + g == ro;
+  }
+  __syncwarp();
+  if (left && right) {
+    if (lane_id() == 0) stcg(E.ext_len + ip - 1, ll + g + rl);
+    __syncwarp();
+    warp_remove_at(E.ext_off, ip, s.n_ext);
+    warp_remove_at(E.ext_len, ip, s.n_ext);
+    s.n_ext -= 1;
+  } else if (left) {
+    if (lane_id() == 0) stcg(E.ext_len + ip - 1, ll + g);
+    __syncwarp();
+  } else if (right) {
+    if (lane_id() == 0) { stcg(E.ext_off + ip, off); stcg(E.ext_len + ip, rl + g); }
+    __syncwarp();
+  } else {
+    warp_insert_at(E.ext_off, ip, s.n_ext, off);
+    warp_insert_at(E.ext_len, ip, s.n_ext, g);
+    s.n_ext += 1;
+  }
+}
+
+// ----------------------------------------------------------- publication
+static_assert(sizeof(sg_record) == 48, "sg_record is 6 x 8 bytes");
+
+__device__ __forceinline__ sg_record rec_load(const Eng& E, uint32_t j) {
+  const uint64_t* p = reinterpret_cast<const uint64_t*>(E.rec + j);
+  uint64_t w[6];
+#pragma unroll
+  for (int i = 0; i < 6; i++) w[i] = ldcg(p + i);
+  sg_record r;
+  memcpy(&r, w, sizeof r);
+  return r;
+}
+
+__device__ __forceinline__ void rec_store(const Eng& E, uint32_t j, const sg_record& r) {
+  uint64_t w[6];
+  memcpy(w, &r, sizeof r);
+  uint64_t* p = reinterpret_cast<uint64_t*>(E.rec + j);
+#pragma unroll
+  for (int i = 0; i < 6; i++) stcg(p + i, w[i]);
+}
+
+// Write a ticket's record to the device log and, in real runs, to the
+// host-mapped copy (status last, after a system fence).
+__device__ __forceinline__ void publish_record(const Eng& E, uint32_t j, const sg_record& r) {
+  __syncwarp();
+  if (lane_id() == 0) {
+    rec_store(E, j, r);
+    if (E.pub_rec) {
+      volatile sg_record* pr = E.pub_rec + j;
+      pr->slot = r.slot;
+      pr->grant_seq = r.grant_seq;
+      pr->grant_t = r.grant_t;
+      pr->offset = r.offset;
+      pr->done_t = r.done_t;
+      pr->arrival_t = r.arrival_t;
+      __threadfence_system();
+      pr->status = r.status;
+    }
+  }
+  __syncwarp();
+}
+
+// Append a granted ticket to the host-mapped grant ring (real runs).
+__device__ __forceinline__ void publish_grant_ring(const Eng& E, Sess& s, uint32_t j) {
+  if (E.pub_ring) {
+    if (lane_id() == 0) {
+      ((volatile uint32_t*)E.pub_ring)[s.ring_tail % s.cap] = j;
+      __threadfence_system();
+      ((volatile uint32_t*)E.pub_hdr)[0] = s.ring_tail + 1;
+    }
+    __syncwarp();
+  }
+  s.ring_tail += 1;
+}
+
+__device__ __forceinline__ void publish_done_count(const Eng& E, const Sess& s) {
+  if (E.pub_hdr && lane_id() == 0) {
+    __threadfence_system();
+    ((volatile uint32_t*)E.pub_hdr)[2] = s.n_done;
+  }
+  __syncwarp();
+}
+
+// ---------------------------------------------------------------- events
+enum : uint32_t { EV_COMPLETE = 0, EV_ARRIVE = 1, EV_TIMEOUT = 2 };
+
+__device__ __forceinline__ bool ev_less(uint64_t ta, uint64_t ka, uint64_t tb, uint64_t kb) {
+  return ta < tb || (ta == tb && ka < kb);
+}
+
+__device__ __forceinline__ void heap_push(EvHeap& H, uint64_t t, uint64_t k, Sess& s) {
+  if (lane_id() == 0) {
+    if (H.n >= H.cap) {
+      s.err |= ERR_HEAP;
+    } else {
+      uint32_t i = H.n++;
+      H.t[i] = t;
+      H.k[i] = k;
+      while (i > 0) {
+        uint32_t p = (i - 1) / 2;
+        if (!ev_less(H.t[i], H.k[i], H.t[p], H.k[p])) break;
+        uint64_t tt = H.t[i], kk = H.k[i];
+        H.t[i] = H.t[p]; H.k[i] = H.k[p]; H.t[p] = tt; H.k[p] = kk;
+        i = p;
+      }
+    }
+  }
+  H.n = __shfl_sync(SG_FULL, H.n, 0);
+  s.err = __shfl_sync(SG_FULL, s.err, 0);
+  __syncwarp();
+}
+
+__device__ __forceinline__ void heap_pop(EvHeap& H) {
+  if (lane_id() == 0) {
+    uint32_t n = --H.n;
+    H.t[0] = H.t[n];
+    H.k[0] = H.k[n];
+    uint32_t i = 0;
+    for (;;) {
+      uint32_t l = 2 * i + 1, r = l + 1, m = i;
+      if (l < n && ev_less(H.t[l], H.k[l], H.t[m], H.k[m])) m = l;
+      if (r < n && ev_less(H.t[r], H.k[r], H.t[m], H.k[m])) m = r;
+      if (m == i) break;
+      uint64_t tt = H.t[i], kk = H.k[i];
+      H.t[i] = H.t[m]; H.k[i] = H.k[m]; H.t[m] = tt; H.k[m] = kk;
+      i = m;
+    }
+  }
+  H.n = __shfl_sync(SG_FULL, H.n, 0);
+  __syncwarp();
+}
+
+// ------------------------------------------------------------ admission
+// Serve ticket j at time t if it count-fits and can be placed.
+// heap != null (replay): push its completion at t + dur[j].
+__device__ __forceinline__ bool try_grant(const Eng& E, Sess& s, uint32_t j, uint64_t t,
+                                          EvHeap* heap, const uint64_t* dur) {
+  uint64_t g = ldcg(E.need_g + j);
+  if (g > s.budget - s.used) return false;              // count test (Sec. III-B)
+  int64_t e = ext_find(E, s, g);
+  if (e < 0) { s.frag += 1; return false; }              // count-fits, cannot be placed
+  uint64_t off = ext_take(E, s, (uint32_t)e, g);
+  s.used += g;
+  if (s.used > s.peak) s.peak = s.used;
+  sg_record r = rec_load(E, j);
+  r.status = ST_RUNNING;
+  r.grant_seq = (int64_t)s.seq;
+  r.grant_t = t;
+  r.offset = off;
+  s.seq += 1;
+  if (lane_id() == 0) {
+    stcg(E.status + j, (uint32_t)ST_RUNNING);
+    stcg(E.blk_done + j, 0u);
+  }
+  publish_record(E, j, r);
+  publish_grant_ring(E, s, j);
+  if (heap) heap_push(*heap, t + dur[j], ((uint64_t)EV_COMPLETE << 32) | j, s);
+  return true;
+}
+
+__device__ __forceinline__ void q_remove(const Eng& E, Sess& s, uint32_t i) {
+  warp_remove_at(E.q, i, s.q_len);
+  s.q_len -= 1;
+}
+
+__device__ __forceinline__ bool is_prio_policy(const Sess& s) {
+  return s.policy == SG_POLICY_PRIO_FIFO || s.policy == SG_POLICY_PRIO_FIRST_FIT;
+}
+
+__device__ __forceinline__ void q_insert(const Eng& E, Sess& s, uint32_t j) {
+  uint32_t pos = s.q_len;
+  if (is_prio_policy(s)) {
+    // stable: after every waiter whose priority value is <= j's
+    int32_t pj = ldcg(E.prio + j);
+    const uint32_t* q = E.q;
+    const int32_t* pr = E.prio;
+    int64_t p = warp_find_first(0, s.q_len, [&](uint32_t i) { return ldcg(pr + ldcg(q + i)) > pj; });
+    pos = p < 0 ? s.q_len : (uint32_t)p;
+  }
+  warp_insert_at(E.q, pos, s.q_len, j);
+  s.q_len += 1;
+  if (lane_id() == 0) stcg(E.status + j, (uint32_t)ST_QUEUED);
+  __syncwarp();
+}
+
+// One notification pass (Sec. V) over the waiting queue at time t.
+__device__ __forceinline__ void policy_pass(const Eng& E, Sess& s, uint64_t t, EvHeap* heap,
+                                            const uint64_t* dur) {
+  s.passes += 1;
+  const uint32_t* q = E.q;
+  const uint64_t* ng = E.need_g;
+  if (s.policy == SG_POLICY_FIFO || s.policy == SG_POLICY_PRIO_FIFO) {
+    // Policy 1 / 3: serve the head while it fits; stop at the first that does not
+    while (s.q_len > 0) {
+      uint32_t h = ldcg(q);
+      if (!try_grant(E, s, h, t, heap, dur)) break;
+      q_remove(E, s, 0);
+    }
+  } else if (s.policy == SG_POLICY_FIRST_FIT) {
+    // Policy 2 (MMU): every waiter that fits, in queue order. Free bytes only
+    // shrink within a pass, so waiters above the free count are skipped.
+    uint32_t i = 0;
+    while (i < s.q_len) {
+      uint64_t freeb = s.budget - s.used;
+      int64_t c = warp_find_first(i, s.q_len, [&](uint32_t k) { return ldcg(ng + ldcg(q + k)) <= freeb; });
+      if (c < 0) break;
+      uint32_t j = ldcg(q + c);
+      if (try_grant(E, s, j, t, heap, dur)) {
+        q_remove(E, s, (uint32_t)c);
+        i = (uint32_t)c;
+      } else {
+        i = (uint32_t)c + 1;
+      }
+    }
+  } else {
+    // Policy 4: first fit inside the highest-priority class present; the next
+    // class is considered only once this one is emptied
+    const int32_t* pr = E.prio;
+    while (s.q_len > 0) {
+      int32_t p = ldcg(pr + ldcg(q));
+      uint32_t i = 0;
+      while (i < s.q_len) {
+        uint32_t j = ldcg(q + i);
+        if (ldcg(pr + j) != p) break;
+        if (try_grant(E, s, j, t, heap, dur)) q_remove(E, s, i);
+        else i += 1;
+      }
+      if (s.q_len > 0 && ldcg(pr + ldcg(q)) == p) break;
+    }
+  }
+}
+
+// ----------------------------------------------------- life-cycle steps
+// Pre-allocation request of ticket j at time t (need_g / need_raw / prio
+// already stored). Returns the ticket's status after the call.
+__device__ __forceinline__ void op_declare(const Eng& E, Sess& s, uint32_t j, uint64_t t,
+                                           int32_t slot, EvHeap* heap, const uint64_t* dur,
+                                           const uint64_t* timeout) {
+  sg_record r;
+  r.status = ST_PENDING; r.slot = slot; r.grant_seq = -1; r.grant_t = 0; r.offset = 0;
+  r.done_t = 0; r.arrival_t = t;
+  uint64_t g = ldcg(E.need_g + j);
+  if (g > s.budget) {
+    // larger than the whole pool: refused at once, never queued
+    r.status = ST_TOO_LARGE;
+    if (lane_id() == 0) stcg(E.status + j, (uint32_t)ST_TOO_LARGE);
+    publish_record(E, j, r);
+    s.n_done += 1;
+    publish_done_count(E, s);
+    return;
+  }
+  if (lane_id() == 0) rec_store(E, j, r);
+  __syncwarp();
+  if ((s.flags & SG_FLAG_FIFO_BYPASS) && s.policy == SG_POLICY_FIFO) {
+    if (try_grant(E, s, j, t, heap, dur)) return;
+  }
+  q_insert(E, s, j);
+  r.status = ST_QUEUED;
+  publish_record(E, j, r);
+  if (heap && timeout && timeout[j] != ~0ull) {
+    uint64_t tt = t + timeout[j];
+    if (tt < t) tt = ~0ull;
+    heap_push(*heap, tt, ((uint64_t)EV_TIMEOUT << 32) | j, s);
+  }
+  policy_pass(E, s, t, heap, dur);
+}
+
+// Post-free of `bytes` declared bytes of ticket j (0 or >= held: all).
+// Returns false (and flags ERR_STATE) if j holds no memory.
+__device__ __forceinline__ bool op_release(const Eng& E, Sess& s, uint32_t j, uint64_t bytes,
+                                           uint64_t t, EvHeap* heap, const uint64_t* dur) {
+  uint32_t st = ldcg(E.status + j);
+  if (st != ST_RUNNING) { s.err |= ERR_STATE; return false; }
+  uint64_t g = ldcg(E.need_g + j);
+  uint64_t raw = ldcg(E.need_raw + j);
+  sg_record r = rec_load(E, j);
+  uint64_t freed_off, freed;
+  bool all = bytes == 0 || bytes >= raw;
+  if (all) {
+    freed_off = r.offset;
+    freed = g;
+    r.status = ST_DONE;
+    r.done_t = t;
+    if (lane_id() == 0) stcg(E.status + j, (uint32_t)ST_DONE);
+    s.n_done += 1;
+  } else {
+    // shrink: keep the granule-rounded remainder at the front of the extent
+    uint64_t keep_raw = raw - bytes;
+    uint64_t keep = (keep_raw + s.granule - 1) / s.granule * s.granule;
+    freed_off = r.offset + keep;
+    freed = g - keep;
+    if (lane_id() == 0) { stcg(E.need_g + j, keep); stcg(E.need_raw + j, keep_raw); }
+  }
+  __syncwarp();
+  if (freed > 0) {
+    ext_give(E, s, freed_off, freed);
+    s.used -= freed;
+  }
+  publish_record(E, j, r);
+  publish_done_count(E, s);
+  policy_pass(E, s, t, heap, dur);
+  return true;
+}
+
+// Withdraw a waiting ticket (timeout). Returns its status after the call.
+__device__ __forceinline__ uint32_t op_cancel(const Eng& E, Sess& s, uint32_t j, uint64_t t,
+                                              EvHeap* heap, const uint64_t* dur) {
+  uint32_t st = ldcg(E.status + j);
+  if (st != ST_QUEUED) return st;
+  const uint32_t* q = E.q;
+  int64_t i = warp_find_first(0, s.q_len, [&](uint32_t k) { return ldcg(q + k) == j; });
+  if (i >= 0) q_remove(E, s, (uint32_t)i);
+  sg_record r = rec_load(E, j);
+  r.status = ST_TIMEOUT;
+  r.done_t = t;
+  if (lane_id() == 0) stcg(E.status + j, (uint32_t)ST_TIMEOUT);
+  s.n_done += 1;
+  publish_record(E, j, r);
+  publish_done_count(E, s);
+  // removing the head can unblock FIFO: notify
+  policy_pass(E, s, t, heap, dur);
+  return ST_TIMEOUT;
+}
+
+// Locked release from a job kernel's last block (warp 0 of it).
+__device__ __forceinline__ void eng_release_locked(const Eng& E, uint32_t j, uint64_t bytes) {
+  if (!eng_lock(E)) return;
+  Sess s = sess_load(E);
+  op_release(E, s, j, bytes, globaltimer_ns(), nullptr, nullptr);
+  sess_store(E, s);
+  eng_unlock(E);
+}
+
+// Release hook carried by a job's final kernel: the last block to finish
+// releases the ticket (post-free on the device, no host round trip).
+struct RelHook {
+  Eng eng;
+  uint32_t ticket;
+  uint32_t active;
+};
+
+__device__ __forceinline__ void job_epilogue(const RelHook& h) {
+  if (!h.active) return;
+  __shared__ uint32_t s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    uint32_t nblk = gridDim.x * gridDim.y * gridDim.z;
+    uint32_t prev = atomicAdd(h.eng.blk_done + h.ticket, 1u);
+    s_last = (prev + 1 == nblk);
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x < 32) {
+    __threadfence();
+    eng_release_locked(h.eng, h.ticket, 0);
+  }
+}
+
+}  // namespace sg

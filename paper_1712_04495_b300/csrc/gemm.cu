@@ -1,0 +1,371 @@
+// BF16 GEMM with FP32 accumulation on the sm_100-family tensor cores
+// (tcgen05): C[M x N] = A[M x K] * Bt[N x K]^T, all K-contiguous.
+//
+// Persistent, warp-specialised, one CTA per SM at most (its shared memory
+// keeps a second one off the SM, so TMEM allocation never waits):
+//   warp 0  TMA producer: 128x64 A tiles and BNx64 B tiles, 128-byte
+//           swizzle, into a ring of kStages shared-memory stages;
+//   warp 1  TMEM allocator and MMA issuer: one elected lane issues
+//           tcgen05.mma (M=128, N=BN, K=16) into one of two TMEM
+//           accumulators and commits to mbarriers;
+//   warps 2-5 epilogue: tcgen05.ld of the accumulator (each warp owns its
+//           32-lane quarter of TMEM), FP32 stores to C; the second
+//           accumulator lets the next tile's MMAs overlap this epilogue.
+// Every mbarrier wait is bounded (globaltimer); a wait that runs out raises
+// a flag, the CTA drains its own in-flight tensor-core work, frees TMEM and
+// returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "engine.cuh"
+#include "jobs.h"
+
+namespace sg {
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kBK = 64;           // 64 bf16 = 128 bytes: one swizzle span
+constexpr int kStages = 4;
+constexpr int kThreadsG = 192;
+constexpr uint64_t kWaitLimitNs = 4000000000ull;
+constexpr int kGroupM = 16;       // tile raster: 16 M-tiles per band
+
+// flags of GEMM kernels that gave up a bounded wait (read by sg_kernel_errors)
+__device__ uint32_t g_tc_err;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait; false if it ran out or another role gave up
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile uint32_t* abort) {
+  if (mbar_try(a, parity)) return true;
+  uint64_t t0 = globaltimer_ns();
+  for (uint32_t it = 0;; it++) {
+    if (mbar_try(a, parity)) return true;
+    if ((it & 63) == 63) {
+      if (*abort) return false;
+      if (globaltimer_ns() - t0 > kWaitLimitNs) {
+        *abort = 1;
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y,
+                                            uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// K-major operand in the 128-byte swizzled layout TMA wrote: rows of 128 B,
+// 8-row groups 1024 B apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);         // start address
+  d |= (uint64_t)1 << 16;                         // leading byte offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset
+  d |= (uint64_t)1 << 46;                         // descriptor version
+  d |= (uint64_t)2 << 61;                         // 128-byte swizzle
+  return d;
+}
+
+// kind::f16 instruction descriptor: BF16 x BF16 -> FP32, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4)            // D format: F32
+         | (1u << 7)          // A format: BF16
+         | (1u << 10)         // B format: BF16
+         | ((uint32_t)(n >> 3) << 17)
+         | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_32cols(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tile_coords(uint32_t t, uint32_t mt, uint32_t nt, uint32_t& m, uint32_t& n) {
+  uint32_t band = t / (kGroupM * nt);
+  uint32_t in = t % (kGroupM * nt);
+  uint32_t rows = mt - band * kGroupM;
+  if (rows > kGroupM) rows = kGroupM;
+  m = band * kGroupM + in % rows;
+  n = in / rows;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kThreadsG, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+              float* __restrict__ C, uint32_t M, uint32_t N, uint32_t K, RelHook hook) {
+  uint32_t* err = &g_tc_err;
+  constexpr uint32_t kABytes = kBM * kBK * 2;
+  constexpr uint32_t kBBytes = BN * kBK * 2;
+  constexpr uint32_t kStageBytes = kABytes + kBBytes;
+  constexpr uint32_t kTmemCols = 2 * BN;          // two accumulators
+  constexpr uint32_t kIdesc = idesc_bf16(kBM, BN);
+
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages], bar_acc_full[2],
+      bar_acc_empty[2], bar_drain;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile uint32_t s_abort;
+
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // 1024-byte aligned ring of stages (128-byte swizzle atoms)
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t ring = (raw + 1023u) & ~1023u;
+
+  const uint32_t mt = M / kBM, nt = N / BN, kb_n = K / kBK;
+  const uint32_t tiles = mt * nt;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; s++) {
+      mbar_init(smem_u32(&bar_full[s]), 1);
+      mbar_init(smem_u32(&bar_empty[s]), 1);
+    }
+    for (int a = 0; a < 2; a++) {
+      mbar_init(smem_u32(&bar_acc_full[a]), 1);
+      mbar_init(smem_u32(&bar_acc_empty[a]), 128);
+    }
+    mbar_init(smem_u32(&bar_drain), 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------ TMA producer
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_a)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_b)) : "memory");
+      uint32_t stage = 0, phase = 0;
+      bool ok = true;
+      for (uint32_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+        uint32_t m, n;
+        tile_coords(t, mt, nt, m, n);
+        for (uint32_t kb = 0; kb < kb_n; kb++) {
+          if (!mbar_wait(smem_u32(&bar_empty[stage]), phase ^ 1u, &s_abort)) { ok = false; break; }
+          const uint32_t sa = ring + stage * kStageBytes;
+          const uint32_t fb = smem_u32(&bar_full[stage]);
+          mbar_expect_tx(fb, kStageBytes);
+          tma_load_2d(sa, &map_a, (int32_t)(kb * kBK), (int32_t)(m * kBM), fb);
+          tma_load_2d(sa + kABytes, &map_b, (int32_t)(kb * kBK), (int32_t)(n * BN), fb);
+          if (++stage == kStages) { stage = 0; phase ^= 1u; }
+        }
+      }
+      if (!ok && err) atomicOr(err, 64u);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------ MMA issuer
+      uint32_t stage = 0, phase = 0, acc = 0, acc_phase = 0;
+      bool ok = true;
+      for (uint32_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+        if (!mbar_wait(smem_u32(&bar_acc_empty[acc]), acc_phase ^ 1u, &s_abort)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t d = tmem + acc * BN;
+        for (uint32_t kb = 0; kb < kb_n; kb++) {
+          if (!mbar_wait(smem_u32(&bar_full[stage]), phase, &s_abort)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t sa = ring + stage * kStageBytes;
+          const uint32_t sb = sa + kABytes;
+#pragma unroll
+          for (uint32_t kk = 0; kk < kBK / 16; kk++) {
+            mma_bf16(d, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32), kIdesc,
+                     (kb | kk) != 0);
+          }
+          mma_commit(smem_u32(&bar_empty[stage]));   // frees the stage when the MMAs finish
+          if (++stage == kStages) { stage = 0; phase ^= 1u; }
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&bar_acc_full[acc]));    // accumulator ready for the epilogue
+        if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
+      }
+      if (!ok) {
+        // give up: let the tensor core finish what was issued before TMEM goes
+        mma_commit(smem_u32(&bar_drain));
+        volatile uint32_t dummy = 0;
+        mbar_wait(smem_u32(&bar_drain), 0, &dummy);
+        if (err) atomicOr(err, 64u);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---------------------------------------------------- epilogue
+    const uint32_t q = warp & 3u;                  // TMEM lane quarter of this warp
+    uint32_t acc = 0, acc_phase = 0;
+    for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+      uint32_t m, n;
+      tile_coords(t, mt, nt, m, n);
+      bool ok = mbar_wait(smem_u32(&bar_acc_full[acc]), acc_phase, &s_abort);
+      if (!__all_sync(SG_FULL, ok)) break;
+      tc_fence_after();
+      const uint32_t row = m * kBM + q * 32 + lane;
+      float* crow = C + (uint64_t)row * N + (uint64_t)n * BN;
+#pragma unroll 1
+      for (uint32_t c = 0; c < BN / 32; c++) {
+        uint32_t r[32];
+        tmem_ld_32cols(tmem + ((q * 32u) << 16) + acc * BN + c * 32, r);
+        float4* dst = reinterpret_cast<float4*>(crow + c * 32);
+#pragma unroll
+        for (int v = 0; v < 8; v++)
+          dst[v] = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
+                               __uint_as_float(r[4 * v + 2]), __uint_as_float(r[4 * v + 3]));
+      }
+      tc_fence_before();
+      mbar_arrive(smem_u32(&bar_acc_empty[acc]));
+      if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                 : "memory");
+  }
+  if (s_abort && threadIdx.x == 0) atomicOr(err, 64u);
+  job_epilogue(hook);
+}
+
+// ---------------------------------------------------------------- host side
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+bool encode_fn() {
+  std::call_once(g_encode_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  return g_encode != nullptr;
+}
+
+// rows x K bf16 matrix, K contiguous; box = box_rows x 64, 128-byte swizzle
+bool make_map(CUtensorMap* map, const void* ptr, uint64_t rows, uint64_t K, uint32_t box_rows) {
+  cuuint64_t dims[2] = {K, rows};
+  cuuint64_t strides[1] = {K * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kBK, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides,
+                        box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int BN>
+int launch_bn(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, uint32_t N, uint32_t K,
+              const RelHook& h, cudaStream_t st) {
+  constexpr uint32_t smem = kStages * (kBM * kBK * 2 + BN * kBK * 2) + 1024;
+  static std::once_flag once;
+  static cudaError_t attr_rc = cudaSuccess;
+  std::call_once(once, [] {
+    attr_rc = cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (attr_rc != cudaSuccess) return SG_ERR_CUDA;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, M, K, kBM) || !make_map(&mb, Bt, N, K, BN)) return SG_ERR_CUDA;
+  uint32_t tiles = (M / kBM) * (N / BN);
+  uint32_t grid = tiles < (uint32_t)num_sms() ? tiles : (uint32_t)num_sms();
+  k_gemm_tc<BN><<<grid, kThreadsG, smem, st>>>(ma, mb, C, M, N, K, h);
+  return cudaPeekAtLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
+}
+
+}  // namespace
+
+int launch_gemm(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, uint32_t N, uint32_t K,
+                const RelHook& h, cudaStream_t st) {
+  if (M == 0 || N == 0 || K == 0 || M % kBM || N % 128 || K % kBK) return SG_ERR_INVALID;
+  if (((uintptr_t)A & 15) || ((uintptr_t)Bt & 15) || ((uintptr_t)C & 15)) return SG_ERR_INVALID;
+  if (!encode_fn()) return SG_ERR_CUDA;
+  if (N % 256 == 0) return launch_bn<256>(A, Bt, C, M, N, K, h, st);
+  return launch_bn<128>(A, Bt, C, M, N, K, h, st);
+}
+
+}  // namespace sg
+
+extern "C" int sg_gemm_bf16(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, uint32_t N,
+                            uint32_t K, void* stream) {
+  if (!A || !Bt || !C) return SG_ERR_INVALID;
+  sg::RelHook h;
+  memset(&h, 0, sizeof h);
+  return sg::launch_gemm(A, Bt, C, M, N, K, h, (cudaStream_t)stream);
+}
+
+extern "C" int sg_kernel_errors(uint32_t* flags_out) {
+  if (!flags_out) return SG_ERR_INVALID;
+  uint32_t v = 0, zero = 0;
+  if (cudaMemcpyFromSymbol(&v, sg::g_tc_err, sizeof v) != cudaSuccess) return SG_ERR_CUDA;
+  if (cudaMemcpyToSymbol(sg::g_tc_err, &zero, sizeof zero) != cudaSuccess) return SG_ERR_CUDA;
+  *flags_out = v;
+  return SG_OK;
+}

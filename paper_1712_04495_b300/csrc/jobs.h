@@ -1,0 +1,39 @@
+// Internal interface between the engine runtime and the job kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "engine.cuh"
+
+namespace sg {
+
+struct SpmvLayout {
+  uint64_t row_ptr, col, val, x, y, scan, total, nchunks;
+  bool ptr64;
+};
+struct GemmLayout {
+  uint64_t A, B, C, total;
+};
+
+int num_sms();
+SpmvLayout spmv_layout(uint64_t rows, uint64_t nnz);
+GemmLayout gemm_layout(uint64_t m, uint64_t n, uint64_t k);
+
+int launch_triad(float* a, const float* b, const float* c, float s, uint64_t n, const RelHook& h,
+                 cudaStream_t st);
+int launch_gen_triad(float* b, float* c, uint64_t n, uint64_t key, cudaStream_t st);
+int launch_spmv(const void* row_ptr, int ptr64, const int32_t* col, const float* val, const float* x,
+                float* y, uint64_t rows, const RelHook& h, cudaStream_t st);
+int launch_gen_spmv(char* base, uint64_t rows, uint64_t nnz, const uint64_t* table, uint64_t key,
+                    uint32_t* err, cudaStream_t st, uint64_t* launches);
+int launch_gen_bf16(uint16_t* out, uint64_t count, uint64_t key, cudaStream_t st);
+int launch_digest(const void* p, uint64_t words, uint64_t* out, const RelHook& h, cudaStream_t st);
+// tcgen05 GEMM (gemm.cu): C = A * Bt^T
+int launch_gemm(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, uint32_t N, uint32_t K,
+                const RelHook& h, cudaStream_t st);
+
+// generator + kernel (+ digest when keep_slot) of one job inside its grant
+int launch_job(const sg_job& job, char* base, const uint64_t* tables, const RelHook& hook,
+               uint64_t* keep_slot, uint32_t* err, cudaStream_t st, uint64_t* launches);
+
+}  // namespace sg

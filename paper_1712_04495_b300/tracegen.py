@@ -63,7 +63,7 @@ JOB_DTYPE = np.dtype([
     ("timeout_ns", "<u8"),
     ("key", "<u8"),
     ("p0", "<u8"),     # triad n | spmv rows | gemm M
-    ("p1", "<u8"),     # spmv nnz | gemm N
+    ("p1", "<u8"),     # spmv nnz capacity | gemm N
     ("p2", "<u4"),     # spmv Poisson table id | gemm K
     ("kind", "<u2"),
     ("prio", "<i2"),
@@ -156,6 +156,18 @@ def row_lengths(len_key: int, rows_idx, table: np.ndarray) -> np.ndarray:
     return np.searchsorted(table, u, side="right").astype(np.int64)
 
 
+def spmv_nnz_cap(rows: int, lam: float) -> int:
+    """Declared capacity for the non-zeros of an SpMV job.
+
+    The row lengths are iid Poisson(lam), so nnz ~ Poisson(rows * lam); the
+    job sizes its col / val arrays for mean + 8 standard deviations + 64
+    (exceeded with probability below 1e-14), the way an application sizes
+    its buffers before it knows the exact count.
+    """
+    mu = rows * lam
+    return int(math.ceil(mu + 8.0 * math.sqrt(mu) + 64))
+
+
 def spmv_nnz(job_key: int, rows: int, table: np.ndarray, chunk: int = 1 << 22) -> int:
     k = stream_key(job_key, 1)
     total = 0
@@ -245,7 +257,7 @@ def _floor64(x):
     return np.maximum(64, (np.asarray(x, np.int64) // 64) * 64)
 
 
-def make_jobs(kinds, sizes, arrivals, seed: int, tables, lam_id=None, prio=None,
+def make_jobs(kinds, sizes, arrivals, seed: int, lams, lam_id=None, prio=None,
               timeout=None) -> np.ndarray:
     n = len(kinds)
     jobs = np.zeros(n, dtype=JOB_DTYPE)
@@ -266,10 +278,10 @@ def make_jobs(kinds, sizes, arrivals, seed: int, tables, lam_id=None, prio=None,
         elif kind == KIND_SPMV:
             rows = int(sizes[j])
             tid = 0 if lam_id is None else int(lam_id[j])
-            nnz = spmv_nnz(int(keys[j]), rows, tables[tid])
-            rec["p0"], rec["p1"], rec["p2"] = rows, nnz, tid
-            need = spmv_layout(rows, nnz)["total"]
-            dur = declared_duration(kind, rows, nnz, 0)
+            cap = spmv_nnz_cap(rows, lams[tid])
+            rec["p0"], rec["p1"], rec["p2"] = rows, cap, tid
+            need = spmv_layout(rows, cap)["total"]
+            dur = declared_duration(kind, rows, int(round(rows * lams[tid])), 0)
         else:
             s = int(sizes[j])
             rec["p0"], rec["p1"], rec["p2"] = s, s, s
@@ -286,7 +298,7 @@ def trace_single_kind_t0(seed: int, n_jobs: int, lo: int, hi: int, budget: int,
     tkey = int(sm64_at(seed ^ 0xC1, 0))
     n = _floor64(_log_uniform_int(_u01(tkey, np.arange(n_jobs)), lo, hi))
     tables = np.stack([poisson_cdf_table(16.0)])
-    jobs = make_jobs([KIND_TRIAD] * n_jobs, n, np.zeros(n_jobs, np.int64), seed, tables)
+    jobs = make_jobs([KIND_TRIAD] * n_jobs, n, np.zeros(n_jobs, np.int64), seed, (16.0,))
     return Trace(name, jobs, budget, tables, (16.0,))
 
 
@@ -332,7 +344,7 @@ def trace_mixed(seed: int = 0, n_jobs: int = 256, rate_per_s: float | None = 200
     else:
         arr = poisson_arrivals(tkey, n_jobs, rate_per_s)
     tables = np.stack([poisson_cdf_table(lam)])
-    jobs = make_jobs(kinds, sizes, arr, seed, tables)
+    jobs = make_jobs(kinds, sizes, arr, seed, (lam,))
     return Trace(name, jobs, budget, tables, (lam,))
 
 
@@ -356,12 +368,12 @@ def trace_c3(seed: int = 0, n_jobs: int = 128, burst: int = 16,
         if kinds[j] == KIND_TRIAD:
             sizes[j] = max(64, target[j] // 12 // 64 * 64)
         elif kinds[j] == KIND_SPMV:
-            sizes[j] = max(1024, target[j] // (8 * 17 + 12))
+            sizes[j] = max(1024, target[j] // (8 * 17 + 12 + 8))
         else:
             sizes[j] = max(128, int(math.isqrt(int(target[j]) // 8)) // 128 * 128)
     arr = (idx // burst) * gap_ns
     tables = np.stack([poisson_cdf_table(16.0)])
-    jobs = make_jobs(kinds, sizes, arr, seed, tables)
+    jobs = make_jobs(kinds, sizes, arr, seed, (16.0,))
     return Trace("pressure128_170GiB", jobs, budget, tables, (16.0,))
 
 
@@ -371,7 +383,7 @@ def trace_c4(seed: int = 0, n_jobs: int = 10_000, budget: int = 2 << 30) -> Trac
     kinds, sizes = _mixed_kinds_sizes(tkey, n_jobs, (4096, 262144), (1024, 65536),
                                       (64, 128, 256, 512))
     tables = np.stack([poisson_cdf_table(8.0)])
-    jobs = make_jobs(kinds, sizes, np.zeros(n_jobs, np.int64), seed, tables)
+    jobs = make_jobs(kinds, sizes, np.zeros(n_jobs, np.int64), seed, (8.0,))
     return Trace("tiny10k_2GiB", jobs, budget, tables, (8.0,))
 
 
