@@ -1,0 +1,387 @@
+"""Benchmark: co-scheduled job execution on one B300 (arXiv 1712.04495).
+
+A step is one pass of the whole path over the mixed 256-job trace (40%
+FP32 triad, 30% CSR SpMV, 30% BF16 GEMM; 16 GiB pool, seed 0): every job
+is declared, admitted by the device engine (first fit), generated and run
+in its grant on a stream slot, and released from its kernel's last block,
+which wakes the waiters. Arrivals are compressed to t = 0 (the saturated
+trace): at the paper-style 200 jobs/s the run is arrival-bound, so that
+literal run is reported beside it.
+
+Prints one JSON line (rank 0). Extra keys: makespan of FIFO / first fit /
+exclusive-serial, p50 / p99 wait, the literal 200 jobs/s run, the roofline
+of the dominant kernel, the oracle's CPU baseline and the end-to-end
+number through host buffers.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1712_04495_b300 import tracegen as tg  # noqa: E402
+
+WORKLOAD = "mixed256_16GiB"
+METRIC = "jobs/s, co-scheduled (first fit) mixed 256-job trace, 16 GiB pool, 1 B300"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained"), "source": "measured"}
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0,
+            "source": "fallback"}
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------- distributed
+def _dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def aggregate(jobs_local: int, seconds_local: float, world: int, backend_ops=None):
+    """Whole-job throughput: jobs over all ranks / slowest rank's time."""
+    if world == 1 or backend_ops is None:
+        return jobs_local / seconds_local, seconds_local
+    total_jobs, max_s = backend_ops(jobs_local, seconds_local)
+    return total_jobs / max_s, max_s
+
+
+def _torch_ops(device):
+    import torch
+    import torch.distributed as dist
+
+    def ops(jobs, secs):
+        t = torch.tensor([float(jobs)], device=device, dtype=torch.float64)
+        s = torch.tensor([secs], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        dist.all_reduce(s, op=dist.ReduceOp.MAX)
+        return float(t.item()), float(s.item())
+    return ops
+
+
+# ----------------------------------------------------------- CPU oracle
+def oracle_sample(trace: tg.Trace, budget_s: float):
+    """The oracle as it stands over a bounded sample of the trace: the
+    admission DES over the whole trace, then each job's CPU reference
+    result in arrival order until budget_s runs out. jobs/s over the jobs
+    whose results were computed."""
+    from oracle import des
+    from oracle import kernels as K
+    t0 = time.perf_counter()
+    des.simulate(trace.jobs, trace.budget, "first_fit")
+    done = 0
+    for j in range(len(trace)):
+        job = trace.jobs[j]
+        kind = int(job["kind"])
+        key = int(job["key"])
+        if kind == tg.KIND_TRIAD:
+            K.triad(key, int(job["p0"]))
+        elif kind == tg.KIND_SPMV:
+            K.spmv(key, int(job["p0"]), trace.tables[int(job["p2"])])
+        else:
+            s = int(job["p0"])
+            K.gemm(key, s, s, s)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return done, el
+
+
+def _threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def reference_arm(args):
+    ws, rank, _ = _dist_env()
+    if rank != 0:
+        return 0
+    trace = tg.trace_c2(saturated=True)
+    per_step = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_sample(trace, per_step)
+    jobs, secs = 0, 0.0
+    for _ in range(args.steps):
+        d, e = oracle_sample(trace, per_step)
+        jobs += d
+        secs += e
+    v = jobs / secs
+    sample = (f"admission DES over all {len(trace)} jobs + CPU reference results of the first "
+              f"jobs in arrival order, {per_step:.0f} s per step")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "jobs/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "policy": "first_fit",
+                                            "arrivals": "t=0 (saturated)"},
+            "cpu_baseline": {"value": v, "unit": "jobs/s", "cores": _threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "jobs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------ kernels
+def kernel_roofline(torch, abi, peaks):
+    """Standalone timing of the job kernels on a torch stream (CUDA events),
+    the same launch configuration the trace uses."""
+    s = torch.cuda.current_stream()
+    out = {}
+    # BF16 GEMM 8192^3
+    M = N = Kd = 8192
+    A = torch.empty(M * Kd, dtype=torch.int16, device="cuda")
+    B = torch.empty(N * Kd, dtype=torch.int16, device="cuda")
+    C = torch.empty(M * N, dtype=torch.float32, device="cuda")
+    assert abi.sg_gen_gemm(A.data_ptr(), B.data_ptr(), M, N, Kd, 42, s.cuda_stream) == 0
+    for _ in range(3):
+        abi.sg_gemm_bf16(A.data_ptr(), B.data_ptr(), C.data_ptr(), M, N, Kd, s.cuda_stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(reps):
+        abi.sg_gemm_bf16(A.data_ptr(), B.data_ptr(), C.data_ptr(), M, N, Kd, s.cuda_stream)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    flops = 2.0 * M * N * Kd
+    tf = flops / (ms * 1e-3) / 1e12
+    out["gemm"] = {"bound": "tensor", "achieved": tf, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                   "frac": tf / peaks["bf16_tflops"], "traffic": None, "ms": ms,
+                   "kernel": "k_gemm_tc<256> 8192^3 bf16", "flops_per_launch": flops}
+    del A, B, C
+    # FP32 triad, n = 64M (768 MB per launch, larger than L2)
+    n = 64 << 20
+    buf = torch.empty(3 * n, dtype=torch.float32, device="cuda")
+    a, b, c = buf[:n], buf[n:2 * n], buf[2 * n:]
+    abi.sg_gen_triad(b.data_ptr(), c.data_ptr(), n, 7, s.cuda_stream)
+    for _ in range(3):
+        abi.sg_triad(a.data_ptr(), b.data_ptr(), c.data_ptr(), 3.0, n, s.cuda_stream)
+    reps = 20
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(reps):
+        abi.sg_triad(a.data_ptr(), b.data_ptr(), c.data_ptr(), 3.0, n, s.cuda_stream)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    gbs = 12.0 * n / (ms * 1e-3) / 1e9
+    out["triad"] = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": gbs / peaks["hbm_gbs"], "traffic": None, "ms": ms,
+                    "kernel": "k_triad n=64M", "bytes_per_launch": 12 * n}
+    del buf
+    torch.cuda.synchronize()
+    return out
+
+
+# ---------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    ws, rank, local = _dist_env()
+    import torch
+    from paper_1712_04495_b300 import abi, runtime
+    torch.cuda.set_device(local)
+    ops = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        ops = _torch_ops(torch.device("cuda", local))
+    peaks = _peaks()
+
+    trace = tg.trace_c2(saturated=True)
+    n = len(trace)
+    sched = runtime.Scheduler(trace.budget, "first_fit")
+    d_jobs = runtime.to_device(trace.jobs)
+    d_tab = runtime.device_tables(trace)
+
+    def step(mode=abi.SG_RUN_SATURATED, s=sched):
+        rc, log, _, st = s.run_trace(d_jobs, d_tab, mode)
+        if rc != abi.SG_OK:
+            raise RuntimeError(f"sg_run_trace: {abi.sg_strerror(rc)} {st}")
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    elapsed, launches, stats = [], 0, []
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        st = step()
+        elapsed.append(st["elapsed_ns"] * 1e-9)
+        launches += st["launches"]
+        stats.append(st)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall0
+    clocks = clk.stop()
+    if ws > 1:
+        torch.distributed.barrier()
+    secs = sum(elapsed)
+    value, max_secs = aggregate(n * args.steps, secs, ws, ops)
+
+    extra = {}
+    if rank == 0:
+        # policies side by side (same trace, same pool)
+        ms = {"first_fit": statistics.median(s["makespan_ns"] for s in stats) / 1e6}
+        fifo = runtime.Scheduler(trace.budget, "fifo", pool=sched.pool)
+        sched_fifo = [step(s=fifo) for _ in range(2)]
+        fifo.shutdown()
+        ms["fifo"] = statistics.median(s["makespan_ns"] for s in sched_fifo) / 1e6
+        ser = [step(abi.SG_RUN_SATURATED | abi.SG_RUN_EXCLUSIVE) for _ in range(2)]
+        ms["exclusive_serial"] = statistics.median(s["makespan_ns"] for s in ser) / 1e6
+        extra["makespan_ms"] = ms
+        extra["makespan_ratio_vs_serial"] = {k: ms[k] / ms["exclusive_serial"] for k in ("first_fit", "fifo")}
+        extra["wait_p50_ms"] = statistics.median(s["wait_p50_ns"] for s in stats) / 1e6
+        extra["wait_p99_ms"] = statistics.median(s["wait_p99_ns"] for s in stats) / 1e6
+        extra["turnaround_p99_ms"] = statistics.median(s["turnaround_p99_ns"] for s in stats) / 1e6
+        extra["peak_used_gib"] = max(s["peak_used"] for s in stats) / 2 ** 30
+        # the literal trace: Poisson arrivals at 200 jobs/s
+        lit = tg.trace_c2(saturated=False)
+        rc, _, _, st = sched.run_trace(runtime.to_device(lit.jobs), runtime.device_tables(lit),
+                                       abi.SG_RUN_TIMED)
+        stl = sched.run_trace(runtime.to_device(lit.jobs), runtime.device_tables(lit),
+                              abi.SG_RUN_TIMED | abi.SG_RUN_EXCLUSIVE)[3]
+        extra["poisson200"] = {"makespan_ms": st["makespan_ns"] / 1e6,
+                               "jobs_per_s": n / (st["makespan_ns"] * 1e-9),
+                               "wait_p50_ms": st["wait_p50_ns"] / 1e6, "wait_p99_ms": st["wait_p99_ns"] / 1e6,
+                               "turnaround_p99_ms": st["turnaround_p99_ns"] / 1e6,
+                               "exclusive_serial_makespan_ms": stl["makespan_ns"] / 1e6,
+                               "arrival_span_ms": int(lit.jobs["arrival_ns"][-1]) / 1e6}
+        # end to end: the same step through host buffers (copies inside the call)
+        e2e_t = []
+        for _ in range(max(2, args.steps // 2)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, rec, _, st = sched.run_trace_host(trace.jobs, d_tab, abi.SG_RUN_SATURATED)
+            e2e_t.append(time.perf_counter() - t0)
+            assert rc == abi.SG_OK
+        extra["e2e"] = {"value": n * len(e2e_t) / sum(e2e_t), "unit": "jobs/s",
+                        "h2d_bytes_per_step": int(trace.jobs.nbytes),
+                        "d2h_bytes_per_step": int(n * abi.RECORD_DTYPE.itemsize)}
+        sched.shutdown()
+        del sched
+        torch.cuda.empty_cache()
+        kr = kernel_roofline(torch, abi, peaks)
+        extra["kernels"] = kr
+        extra["roofline"] = {k: kr["gemm"][k] for k in ("bound", "achieved", "peak", "unit", "frac",
+                                                        "traffic")}
+        extra["roofline"]["kernel"] = kr["gemm"]["kernel"]
+        extra["roofline"]["peak_source"] = peaks["source"] + " (burst, kernel timed alone)"
+        if not args.no_cpu_baseline:
+            d, e = oracle_sample(trace, 20.0)
+            extra["cpu_baseline"] = {"value": d / e, "unit": "jobs/s", "cores": _threads(),
+                                     "kind": "oracle",
+                                     "sample": f"admission DES of all {n} jobs + CPU reference results "
+                                               f"of the first {d} jobs in arrival order ({e:.1f} s)"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "jobs/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * max_secs / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int64 admission; f32 triad/spmv; bf16 in, f32 acc gemm",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD + "_t0", "jobs": n, "pool_gib": 16, "policy": "first_fit",
+                           "arrivals": "t=0 (saturated)", "seed": 0,
+                           "l2": "inputs larger than L2 (about 50 GB of job data per step)",
+                           "parallelism": f"replicas x{ws}"},
+                "gpu_launches": launches, "clocks": clocks, "wall_s": wall}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -102,7 +102,7 @@ typedef struct sg_config {
     uint32_t policy;       /* SG_POLICY_*                                  */
     uint32_t flags;        /* SG_FLAG_*                                    */
     uint32_t max_tickets;  /* capacity of the ticket table (0 = 1 << 17)   */
-    uint32_t n_streams;    /* stream slots for sg_run_trace (0 = 48)       */
+    uint32_t n_streams;    /* stream slots for sg_run_trace (0 = 32)       */
     uint64_t granule;      /* allocation granule, power of two >= 256 (0 = 256) */
 } sg_config;
 

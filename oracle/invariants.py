@@ -163,7 +163,9 @@ def check_log(jobs, out, budget, policy, granule=256, exclusive=False, replay=Tr
             assert status[j] == ST_DONE, f"job {j} lost (status {status[j]})"
     peak = check_no_overcommit(gt, dt, needg, budget, done)
     check_disjoint(gt, dt, off, needg, budget, done)
-    check_placement(seq, gt, dt, off, needg, budget, done)
+    if replay:
+        # needs exact event times; a real run's clock can tie distinct events
+        check_placement(seq, gt, dt, off, needg, budget, done)
     if policy in ("fifo",):
         check_fifo_order(arrival, seq, gt, done)
     if policy in ("fifo", "first_fit") and np.all(status != ST_TIMEOUT) and replay:

@@ -296,7 +296,7 @@ extern "C" int sg_init(sg_ctx** out, void* dev_pool, uint64_t pool_bytes, const 
   c->policy = d.policy;
   c->flags = d.flags;
   c->cap = cap;
-  c->n_slots = d.n_streams ? d.n_streams : 48;
+  c->n_slots = d.n_streams ? d.n_streams : 32;
   c->rel_enq.assign(cap, 0);
   int rc = SG_ERR_CUDA;
   do {

@@ -1,0 +1,165 @@
+"""Job-kernel parity against the CPU oracle: triad bit-exact, SpMV within
+1e-5 (per row, relative to sum |a_ij x_j|), BF16 GEMM within 2e-2 relative
+Frobenius error of the fp64 result (and far tighter for small K)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import kernels as K
+from paper_1712_04495_b300 import tracegen as tg
+
+pytestmark = pytest.mark.gpu
+
+
+def _abi():
+    from paper_1712_04495_b300 import abi
+    return abi
+
+
+def _f32(t):
+    return t.cpu().numpy()
+
+
+@pytest.mark.parametrize("n,skew", [(1, 0), (3, 1), (64, 0), (1000, 1), (100003, 0),
+                                    (1 << 20, 0), ((1 << 20) + 5, 3)])
+def test_triad_bit_exact(n, skew):
+    abi = _abi()
+    key = 0xABCDEF + n
+    buf = torch.zeros(3 * n + 8, dtype=torch.float32, device="cuda")
+    a = buf[skew:skew + n]
+    b = buf[skew + n:skew + 2 * n]
+    c = buf[skew + 2 * n:skew + 3 * n]
+    assert abi.sg_gen_triad(b.data_ptr(), c.data_ptr(), n, key) == 0
+    assert abi.sg_triad(a.data_ptr(), b.data_ptr(), c.data_ptr(), 3.0, n) == 0
+    torch.cuda.synchronize()
+    rb, rc = K.triad_inputs(key, np.arange(n, dtype=np.uint64))
+    assert np.array_equal(_f32(b).view(np.uint32), rb.view(np.uint32))
+    assert np.array_equal(_f32(c).view(np.uint32), rc.view(np.uint32))
+    assert np.array_equal(_f32(a).view(np.uint32), K.triad(key, n).view(np.uint32))
+
+
+def test_triad_full_size_sampled():
+    abi = _abi()
+    n = 64 << 20
+    key = 77
+    buf = torch.empty(3 * n, dtype=torch.float32, device="cuda")
+    a, b, c = buf[:n], buf[n:2 * n], buf[2 * n:]
+    assert abi.sg_gen_triad(b.data_ptr(), c.data_ptr(), n, key) == 0
+    assert abi.sg_triad(a.data_ptr(), b.data_ptr(), c.data_ptr(), 3.0, n) == 0
+    torch.cuda.synchronize()
+    idx = np.unique(np.concatenate([np.arange(8), n - 1 - np.arange(8),
+                                    np.random.default_rng(0).integers(0, n, 4096)]))
+    got = a[torch.from_numpy(idx).cuda()].cpu().numpy()
+    assert np.array_equal(got.view(np.uint32), K.triad_sampled(key, idx).view(np.uint32))
+
+
+def _spmv_case(rows, lam, key):
+    abi = _abi()
+    table = tg.poisson_cdf_table(lam)
+    cap = tg.spmv_nnz_cap(rows, lam)
+    lay = tg.spmv_layout(rows, cap)
+    base = torch.zeros(lay["total"], dtype=torch.uint8, device="cuda")
+    d_table = torch.from_numpy(table.view(np.int64).copy()).cuda()
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert abi.sg_gen_spmv(base.data_ptr(), rows, cap, d_table.data_ptr(), key, err.data_ptr()) == 0
+    p = base.data_ptr()
+    assert abi.sg_spmv(p + lay["row_ptr"], lay["ptr64"], p + lay["col"], p + lay["val"], p + lay["x"],
+                       p + lay["y"], rows) == 0
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    raw = base.cpu().numpy()
+    ptr_t = np.int64 if lay["ptr64"] else np.int32
+    return raw, lay, ptr_t, table
+
+
+@pytest.mark.parametrize("rows,lam", [(1, 16.0), (7, 16.0), (1000, 8.0), (100003, 16.0)])
+def test_spmv_generator_and_product(rows, lam):
+    key = 991 + rows
+    raw, lay, ptr_t, table = _spmv_case(rows, lam, key)
+    ptr, col, val, x = K.spmv_csr(key, rows, table)
+    nnz = int(ptr[-1])
+    g_ptr = raw[lay["row_ptr"]:].view(ptr_t)[: rows + 1].astype(np.int64)
+    assert np.array_equal(g_ptr, ptr)
+    assert np.array_equal(raw[lay["col"]:].view(np.int32)[:nnz].astype(np.int64), col)
+    assert np.array_equal(raw[lay["x"]:].view(np.float32)[:rows].view(np.uint32), x.view(np.uint32))
+    g_val = raw[lay["val"]:].view(np.float32)[:nnz].astype(np.float64)
+    # Box-Muller in fp32 on the GPU vs fp64 rounded once here
+    assert np.all(np.abs(g_val - val.astype(np.float64)) <= 4e-6 * np.maximum(1.0, np.abs(val)))
+    y, mag = K.spmv(key, rows, table)
+    gy = raw[lay["y"]:].view(np.float32)[:rows].astype(np.float64)
+    assert np.all(np.abs(gy - y) <= 1e-5 * mag + 1e-30)
+    if np.linalg.norm(y) > 0:
+        assert np.linalg.norm(gy - y) / np.linalg.norm(y) <= 1e-5
+
+
+def test_spmv_full_size_sampled():
+    rows, lam, key = 10_000_000, 16.0, 5
+    raw, lay, ptr_t, table = _spmv_case(rows, lam, key)
+    sample = np.unique(np.concatenate([[0, 1, rows - 1],
+                                       np.random.default_rng(1).integers(0, rows, 2000)]))
+    y, mag, ptr = K.spmv_sampled(key, rows, table, sample)
+    g_ptr = raw[lay["row_ptr"]:].view(ptr_t)[: rows + 1].astype(np.int64)
+    assert np.array_equal(g_ptr, ptr)
+    gy = raw[lay["y"]:].view(np.float32)[sample].astype(np.float64)
+    assert np.all(np.abs(gy - y) <= 1e-5 * mag + 1e-30)
+
+
+def _gemm(M, N, Kd, key):
+    abi = _abi()
+    A = torch.empty(M * Kd, dtype=torch.int16, device="cuda")
+    Bt = torch.empty(N * Kd, dtype=torch.int16, device="cuda")
+    C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    assert abi.sg_gen_gemm(A.data_ptr(), Bt.data_ptr(), M, N, Kd, key) == 0
+    assert abi.sg_gemm_bf16(A.data_ptr(), Bt.data_ptr(), C.data_ptr(), M, N, Kd) == 0
+    torch.cuda.synchronize()
+    assert abi.sg_kernel_errors() == 0
+    return A, Bt, C
+
+
+@pytest.mark.parametrize("M,N,Kd", [(128, 128, 64), (128, 256, 128), (256, 384, 192),
+                                    (512, 512, 512), (1024, 1024, 1024), (384, 640, 2048)])
+def test_gemm_matches_fp64(M, N, Kd):
+    key = 1234 + M + N + Kd
+    A, Bt, C = _gemm(M, N, Kd, key)
+    # the inputs are the oracle's bf16 values
+    ga = A.cpu().numpy().view(np.uint16)
+    ra = tg.bf16_bits_rne(tg.uniform_pm1_f32(tg.sm64_at(tg.stream_key(key, 1), np.arange(M * Kd))))
+    assert np.array_equal(ga, ra)
+    ref = K.gemm(key, M, N, Kd)
+    got = C.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(got))
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert rel <= 2e-2
+    # fp32 accumulation of exact bf16 products: error ~ sqrt(K) * 2^-24
+    assert rel <= 1e-5, rel
+
+
+def test_gemm_full_size_sampled():
+    M = N = Kd = 8192
+    key = 42
+    A, Bt, C = _gemm(M, N, Kd, key)
+    rng = np.random.default_rng(2)
+    ii = np.concatenate([[0, M - 1, 0, M - 1], rng.integers(0, M, 1020)])
+    jj = np.concatenate([[0, N - 1, N - 1, 0], rng.integers(0, N, 1020)])
+    ref = K.gemm_sampled(key, M, N, Kd, ii, jj)
+    got = C[torch.from_numpy(ii).cuda(), torch.from_numpy(jj).cuda()].cpu().numpy().astype(np.float64)
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert rel <= 2e-2 and rel <= 1e-5, rel
+
+
+def test_gemm_rejects_bad_shapes():
+    abi = _abi()
+    assert abi.sg_gemm_bf16(16, 16, 16, 100, 128, 64) == abi.SG_ERR_INVALID
+    assert abi.sg_gemm_bf16(16, 16, 16, 128, 128, 63) == abi.SG_ERR_INVALID
+
+
+def test_digest_is_order_free_sum():
+    abi = _abi()
+    n = 10007
+    x = torch.randn(n, device="cuda")
+    out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    assert abi.sg_digest(x.data_ptr(), n, out.data_ptr()) == 0
+    w = x.cpu().numpy().view(np.uint32).astype(np.uint64)
+    with np.errstate(over="ignore"):
+        ref = np.sum(tg.mix64((np.arange(n, dtype=np.uint64) << np.uint64(32)) | w), dtype=np.uint64)
+    assert int(out.item()) & ((1 << 64) - 1) == int(ref)
