@@ -200,6 +200,27 @@ int sg_replay(const sg_job* jobs_dev, uint32_t n, uint64_t budget, uint64_t gran
               uint32_t policy, uint32_t flags, uint32_t exclusive, sg_record* log_dev,
               void* workspace_dev, uint64_t* stats_dev, void* stream);
 
+/* sg_replay without any allocation. The paper has no counterpart; this
+ * entry point is for callers that cannot call cudaMalloc: a process that has
+ * already handed all of its device memory to the pool this library
+ * schedules (any further allocation would fall outside the budget the
+ * scheduler accounts for, and could fail or push a co-scheduled job out of
+ * memory), and latency-critical host loops that must not enter the CUDA
+ * allocator. The caller passes the jobs, the log and the stats as for
+ * sg_replay; the workspace is a fixed array of 1600 KiB inside the
+ * library's device image, which every GPU that loads the library holds
+ * until the process exits. Up to SG_REPLAY_NOALLOC_MAX_JOBS jobs; larger
+ * traces get SG_ERR_TOO_LARGE and nothing runs. The first call on each
+ * device looks up the array's device address (make that first call before
+ * any stream capture). All calls share the array and it keeps the last
+ * call's contents; the replay initialises what it reads, so no clearing is
+ * needed, but calls that overlap on the GPU race on it: order them on one
+ * stream. */
+#define SG_REPLAY_NOALLOC_MAX_JOBS 16384u
+int sg_replay_noalloc(const sg_job* jobs_dev, uint32_t n, uint64_t budget, uint64_t granule,
+                      uint32_t policy, uint32_t flags, uint32_t exclusive, sg_record* log_dev,
+                      uint64_t* stats_dev, void* stream);
+
 /* Flags raised by job kernels that gave up a bounded wait (the tcgen05
  * GEMM's mbarrier waits), OR-ed since the last call, then cleared.
  * Synchronous (device-wide). */

@@ -77,6 +77,7 @@ _SIGS = {
     "sg_run_trace": ([_P, _P, _U32, _P, _U32, _P, _P, ctypes.POINTER(SgRunStats)], ctypes.c_int),
     "sg_replay_workspace_bytes": ([_U32], _U64),
     "sg_replay": ([_P, _U32, _U64, _U64, _U32, _U32, _U32, _P, _P, _P, _P], ctypes.c_int),
+    "sg_replay_noalloc": ([_P, _U32, _U64, _U64, _U32, _U32, _U32, _P, _P, _P], ctypes.c_int),
     "sg_kernel_errors": ([ctypes.POINTER(_U32)], ctypes.c_int),
     "sg_device_error": ([_P], _U32),
     "sg_strerror": ([ctypes.c_int], ctypes.c_char_p),
@@ -185,6 +186,16 @@ def sg_replay(jobs_ptr: int, n: int, budget: int, granule: int, policy, flags: i
     pol = POLICIES[policy] if isinstance(policy, str) else int(policy)
     return lib().sg_replay(jobs_ptr, n, budget, granule, pol, flags, int(bool(exclusive)), log_ptr,
                            ws_ptr, stats_ptr or None, stream)
+
+
+SG_REPLAY_NOALLOC_MAX_JOBS = 16384
+
+
+def sg_replay_noalloc(jobs_ptr: int, n: int, budget: int, granule: int, policy, flags: int,
+                      exclusive: bool, log_ptr: int, stats_ptr: int = 0, stream: int = 0) -> int:
+    pol = POLICIES[policy] if isinstance(policy, str) else int(policy)
+    return lib().sg_replay_noalloc(jobs_ptr, n, budget, granule, pol, flags, int(bool(exclusive)),
+                                   log_ptr, stats_ptr or None, stream)
 
 
 def sg_kernel_errors() -> int:

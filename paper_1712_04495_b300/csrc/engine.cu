@@ -655,3 +655,50 @@ extern "C" const char* sg_strerror(int code) {
     default: return "unrecognised code";
   }
 }
+
+// ======================================================= replay, no allocation
+// The same replay as sg_replay, with its workspace in a fixed array that is
+// part of this library's device image instead of caller-provided memory.
+namespace {
+
+constexpr uint32_t kNoAllocMaxJobs = 16384;
+constexpr uint64_t kNoAllocBytes = 1600ull * 1024;   // >= sg_replay_workspace_bytes(16384)
+
+// Shared by every call on a device; kept until the process exits.
+static __device__ __align__(256) unsigned char g_replay_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 128;
+std::mutex g_scratch_mu;
+void* g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of the array on the current device, looked up once per
+// device. In host code the array's name is only a stand-in for it.
+int scratch_address(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SG_ERR_CUDA;
+  if (dev < 0 || dev >= kMaxDevices) return SG_ERR_INVALID;
+  std::lock_guard<std::mutex> g(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_replay_scratch) != cudaSuccess || !p) return SG_ERR_CUDA;
+    g_scratch_ptr[dev] = p;
+  }
+  *out = g_scratch_ptr[dev];
+  return SG_OK;
+}
+
+}  // namespace
+
+extern "C" int sg_replay_noalloc(const sg_job* jobs_dev, uint32_t n, uint64_t budget, uint64_t granule,
+                                 uint32_t policy, uint32_t flags, uint32_t exclusive, sg_record* log_dev,
+                                 uint64_t* stats_dev, void* stream) {
+  if (n > kNoAllocMaxJobs || sg_replay_workspace_bytes(n) > kNoAllocBytes) return SG_ERR_TOO_LARGE;
+  if (n == 0) return SG_OK;
+  if (!jobs_dev || !log_dev) return SG_ERR_INVALID;
+  void* ws = nullptr;
+  int rc = scratch_address(&ws);
+  if (rc != SG_OK) return rc;
+  // the replay kernels initialise every part of the workspace they read, so
+  // the previous call's contents need no clearing
+  return sg_replay(jobs_dev, n, budget, granule, policy, flags, exclusive, log_dev, ws, stats_dev, stream);
+}
