@@ -250,6 +250,33 @@ def kernel_roofline(torch, abi, peaks):
                     "frac": gbs / peaks["hbm_gbs"], "traffic": None, "ms": ms,
                     "kernel": "k_triad n=64M", "bytes_per_launch": 12 * n}
     del buf
+    # FP32 CSR SpMV, 1e7 rows, Poisson(16) non-zeros per row
+    rows, lam = 10_000_000, 16.0
+    cap = tg.spmv_nnz_cap(rows, lam)
+    lay = tg.spmv_layout(rows, cap)
+    base = torch.empty(lay["total"], dtype=torch.uint8, device="cuda")
+    tab = torch.from_numpy(tg.poisson_cdf_table(lam).view(np.int64).copy()).cuda()
+    p = base.data_ptr()
+    abi.sg_gen_spmv(p, rows, cap, tab.data_ptr(), 5, 0, s.cuda_stream)
+    torch.cuda.synchronize()
+    nnz = int(base[lay["row_ptr"] + 4 * rows:lay["row_ptr"] + 4 * rows + 4].view(torch.int32).item())
+    args_ = (p + lay["row_ptr"], False, p + lay["col"], p + lay["val"], p + lay["x"], p + lay["y"], rows,
+             s.cuda_stream)
+    for _ in range(3):
+        abi.sg_spmv(*args_)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(reps):
+        abi.sg_spmv(*args_)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    alg = 4 * (rows + 1) + 8 * nnz + 8 * rows
+    gbs = alg / (ms * 1e-3) / 1e9
+    out["spmv"] = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                   "frac": gbs / peaks["hbm_gbs"], "traffic": None, "ms": ms,
+                   "kernel": "k_spmv<int> rows=1e7 nnz/row~Poisson(16)", "bytes_per_launch": alg}
+    del base
     torch.cuda.synchronize()
     return out
 

@@ -49,8 +49,8 @@ def spmv_csr(key: int, rows: int, table):
     """CSR arrays (row_ptr int64, col int64, val fp32) and x (fp32)."""
     ptr = spmv_row_ptr(key, rows, table)
     e = np.arange(ptr[-1], dtype=np.uint64)
-    col = tg.column_index(tg.sm64_at(tg.stream_key(key, 2), e), rows)
-    val = tg.normal_f32(tg.sm64_at(tg.stream_key(key, 3), e))
+    col = tg.spmv_columns(tg.stream_key(key, 2), e, rows)
+    val = tg.spmv_values(tg.stream_key(key, 3), e)
     x = tg.uniform_pm1_f32(tg.sm64_at(tg.stream_key(key, 4), np.arange(rows, dtype=np.uint64)))
     return ptr, col, val, x
 
@@ -78,8 +78,8 @@ def spmv_sampled(key: int, rows: int, table, sample_rows):
     mag = np.zeros(len(sample_rows))
     for t, r in enumerate(sample_rows):
         e = np.arange(ptr[r], ptr[r + 1], dtype=np.uint64)
-        col = tg.column_index(tg.sm64_at(kc, e), rows)
-        val = tg.normal_f32(tg.sm64_at(kv, e)).astype(np.float64)
+        col = tg.spmv_columns(kc, e, rows)
+        val = tg.spmv_values(kv, e).astype(np.float64)
         x = tg.uniform_pm1_f32(tg.sm64_at(kx, col.astype(np.uint64))).astype(np.float64)
         y[t] = float(np.sum(val * x))
         mag[t] = float(np.sum(np.abs(val * x)))

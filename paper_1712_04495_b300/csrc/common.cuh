@@ -33,16 +33,20 @@ __device__ __forceinline__ float uniform_pm1(uint64_t h) {
   return __fsub_rn(__fmul_rn((float)(uint32_t)(h >> 40), 0x1p-23f), 1.0f);
 }
 
-// N(0,1) by Box-Muller on two 24-bit uniforms taken from one hash
-__device__ __forceinline__ float normal01(uint64_t h) {
+// Two N(0,1) values by Box-Muller on two 24-bit uniforms taken from one
+// hash: r cos(2 pi u2) (even element of a pair) and r sin(2 pi u2) (odd).
+__device__ __forceinline__ float2 normal_pair(uint64_t h) {
   float u1 = (float)((uint32_t)(h >> 40) + 1u) * 0x1p-24f;            // (0, 1]
   float u2 = (float)((uint32_t)(h >> 16) & 0xFFFFFFu) * 0x1p-24f;     // [0, 1)
-  return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+  float r = sqrtf(-2.0f * logf(u1));
+  float sn, cs;
+  sincospif(2.0f * u2, &sn, &cs);
+  return make_float2(r * cs, r * sn);
 }
 
-// column index in [0, n): multiply-shift of the high 32 bits
-__device__ __forceinline__ uint32_t column_of(uint64_t h, uint64_t n) {
-  return (uint32_t)(((h >> 32) * n) >> 32);
+// column index in [0, n) from 32 random bits: multiply-shift
+__device__ __forceinline__ uint32_t column_of32(uint32_t w, uint64_t n) {
+  return (uint32_t)(((uint64_t)w * n) >> 32);
 }
 
 // bf16 bits of an fp32 value, round to nearest, ties to even (finite input)

@@ -236,6 +236,7 @@ struct sg_ctx {
   uint32_t next_ticket = 0;
   std::vector<uint8_t> rel_enq;  // a full release is already enqueued
   cudaStream_t ctrl = nullptr;
+  uint32_t n_hp = 8;             // high-priority slots [n_slots, n_slots + n_hp): GEMM jobs
   std::vector<cudaStream_t> slots;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<cudaEvent_t> slot_ev;
@@ -325,11 +326,16 @@ extern "C" int sg_init(sg_ctx** out, void* dev_pool, uint64_t pool_bytes, const 
     int lo = 0, hi = 0;
     if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) break;
     if (cudaStreamCreateWithPriority(&c->ctrl, cudaStreamNonBlocking, hi) != cudaSuccess) break;
-    c->slots.assign(c->n_slots, nullptr);
-    c->slot_ev.assign(c->n_slots, nullptr);
+    // GEMM jobs get streams one step above the others: their persistent
+    // CTAs (one per SM) are then placed ahead of pending memory-bound blocks
+    const int gemm_prio = hi < lo ? hi + 1 : hi;
+    const uint32_t total = c->n_slots + c->n_hp;
+    c->slots.assign(total, nullptr);
+    c->slot_ev.assign(total, nullptr);
     bool ok = true;
-    for (uint32_t i = 0; i < c->n_slots && ok; i++) {
-      ok = cudaStreamCreateWithPriority(&c->slots[i], cudaStreamNonBlocking, lo) == cudaSuccess &&
+    for (uint32_t i = 0; i < total && ok; i++) {
+      ok = cudaStreamCreateWithPriority(&c->slots[i], cudaStreamNonBlocking, i < c->n_slots ? lo : gemm_prio) ==
+               cudaSuccess &&
            cudaEventCreateWithFlags(&c->slot_ev[i], cudaEventDisableTiming) == cudaSuccess;
     }
     if (!ok) break;
@@ -476,10 +482,12 @@ extern "C" int sg_run_trace(sg_ctx* c, const sg_job* jobs, uint32_t n, const uin
   }
   CK(cudaStreamSynchronize(c->ctrl));
   uint64_t launches = 0;
-  std::vector<int32_t> slot_ticket(c->n_slots, -1);
-  std::vector<uint8_t> slot_used(c->n_slots, 0);
-  std::vector<uint32_t> pending;
+  const uint32_t n_all = (uint32_t)c->slots.size();
+  std::vector<int32_t> slot_ticket(n_all, -1);
+  std::vector<uint8_t> slot_used(n_all, 0);
+  std::vector<uint32_t> pending, pend_hp;
   pending.reserve(n);
+  pend_hp.reserve(n);
   uint32_t ring_head = 0, failed = 0;
   CK(cudaEventRecord(c->ev0, c->ctrl));
   uint32_t declared = 0;
@@ -492,8 +500,8 @@ extern "C" int sg_run_trace(sg_ctx* c, const sg_job* jobs, uint32_t n, const uin
   }
   uint64_t last_progress = now_ns();
   uint32_t last_done = 0;
-  size_t pend_pos = 0;
-  uint32_t rr = 0;
+  size_t pend_pos = 0, pend_pos_hp = 0;
+  uint32_t rr = 0, rr_hp = 0;
   while (true) {
     if (timed && declared < n) {
       uint64_t el = now_ns() - t0;
@@ -507,41 +515,51 @@ extern "C" int sg_run_trace(sg_ctx* c, const sg_job* jobs, uint32_t n, const uin
       }
     }
     uint32_t tail = c->h_hdr[0];
-    while (ring_head < tail) pending.push_back((uint32_t)c->h_ring[(ring_head++) % c->cap]);
-    while (pend_pos < pending.size()) {
-      // a slot whose last job has released its memory (or was never used)
-      int slot = -1;
-      for (uint32_t k = 0; k < c->n_slots; k++) {
-        uint32_t s = (rr + k) % c->n_slots;
-        int32_t tk = slot_ticket[s];
-        if (tk < 0 || (uint32_t)c->h_rec[tk].status >= SG_ST_DONE) { slot = (int)s; break; }
+    while (ring_head < tail) {
+      uint32_t t = (uint32_t)c->h_ring[(ring_head++) % c->cap];
+      (hj[t].kind == SG_KIND_GEMM && c->n_hp > 0 ? pend_hp : pending).push_back(t);
+    }
+    // launch granted jobs on slots whose last job has released its memory
+    // (or were never used); GEMM jobs take the high-priority slots
+    for (int pool = 0; pool < 2; pool++) {
+      std::vector<uint32_t>& q = pool ? pend_hp : pending;
+      size_t& pos = pool ? pend_pos_hp : pend_pos;
+      const uint32_t first = pool ? c->n_slots : 0, cnt = pool ? c->n_hp : c->n_slots;
+      uint32_t& cursor = pool ? rr_hp : rr;
+      while (pos < q.size()) {
+        int slot = -1;
+        for (uint32_t k = 0; k < cnt; k++) {
+          uint32_t s = first + (cursor + k) % cnt;
+          int32_t tk = slot_ticket[s];
+          if (tk < 0 || (uint32_t)c->h_rec[tk].status >= SG_ST_DONE) { slot = (int)s; break; }
+        }
+        if (slot < 0) break;
+        cursor = (uint32_t)slot - first + 1;
+        const uint32_t t = q[pos++];
+        RelHook h;
+        h.eng = c->eng;
+        h.ticket = t;
+        h.active = 1;
+        char* base = c->pool + c->h_rec[t].offset;
+        int lrc = launch_job(hj[t], base, tables_dev, h, want_keep ? c->d_keep + t : nullptr, c->d_err,
+                             c->slots[slot], &launches);
+        if (lrc != SG_OK) {
+          // the job cannot run: give its memory back so no waiter is lost
+          cudaGetLastError();
+          k_release<<<1, 32, 0, c->slots[slot]>>>(c->eng, t, 0);
+          launches++;
+          failed++;
+        }
+        c->rel_enq[t] = 1;
+        slot_ticket[slot] = (int32_t)t;
+        slot_used[slot] = 1;
       }
-      if (slot < 0) break;
-      rr = (uint32_t)slot + 1;
-      uint32_t t = pending[pend_pos++];
-      RelHook h;
-      h.eng = c->eng;
-      h.ticket = t;
-      h.active = 1;
-      char* base = c->pool + c->h_rec[t].offset;
-      int lrc = launch_job(hj[t], base, tables_dev, h, want_keep ? c->d_keep + t : nullptr, c->d_err,
-                           c->slots[slot], &launches);
-      if (lrc != SG_OK) {
-        // the job cannot run: give its memory back so no waiter is lost
-        cudaGetLastError();
-        k_release<<<1, 32, 0, c->slots[slot]>>>(c->eng, t, 0);
-        launches++;
-        failed++;
-      }
-      c->rel_enq[t] = 1;
-      slot_ticket[slot] = (int32_t)t;
-      slot_used[slot] = 1;
     }
     uint32_t done = c->h_hdr[2];
     if (done >= n && declared >= n) break;
     if (c->h_hdr[1]) break;
     uint64_t tn = now_ns();
-    if (done != last_done || ring_head != pend_pos) {
+    if (done != last_done || ring_head != pend_pos + pend_pos_hp) {
       last_done = done;
       last_progress = tn;
     } else if (tn - last_progress > 120ull * 1000000000ull) {
@@ -549,7 +567,7 @@ extern "C" int sg_run_trace(sg_ctx* c, const sg_job* jobs, uint32_t n, const uin
     }
     for (int i = 0; i < 16; i++) cpu_relax();
   }
-  for (uint32_t s = 0; s < c->n_slots; s++) {
+  for (uint32_t s = 0; s < n_all; s++) {
     if (!slot_used[s]) continue;
     CK(cudaEventRecord(c->slot_ev[s], c->slots[s]));
     CK(cudaStreamWaitEvent(c->ctrl, c->slot_ev[s], 0));

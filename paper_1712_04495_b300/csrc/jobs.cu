@@ -8,7 +8,6 @@
 namespace sg {
 
 constexpr int kThreads = 256;
-constexpr int kBlocksPerSm = 4;      // half the SM's thread slots per job kernel
 constexpr int kRowsPerChunk = 4096;  // SpMV CSR build: rows per scan chunk
 
 static int g_num_sms = 0;
@@ -24,11 +23,16 @@ int num_sms() {
   return g_num_sms;
 }
 
-static unsigned grid_for(uint64_t work_items, int per_block) {
+// Short-lived blocks with a fixed amount of work each (the loops stay
+// grid-stride, so any grid is correct). Blocks that retire every few
+// microseconds let the block scheduler interleave the blocks of every job
+// running at the time, and let a co-running GEMM place its persistent CTAs
+// as soon as an SM has room, instead of waiting for whole kernels to drain.
+static unsigned grid_for(uint64_t work_items, uint64_t per_block) {
   uint64_t want = (work_items + per_block - 1) / per_block;
-  uint64_t cap = (uint64_t)num_sms() * kBlocksPerSm;
   if (want < 1) want = 1;
-  return (unsigned)(want < cap ? want : cap);
+  if (want > (1ull << 30)) want = 1ull << 30;
+  return (unsigned)want;
 }
 
 // ------------------------------------------------------------------ triad
@@ -94,47 +98,73 @@ __global__ void __launch_bounds__(kThreads) k_gen_triad(float* __restrict__ b, f
 }
 
 // ------------------------------------------------------------------- SpMV
-// Eight lanes per row, four rows per warp step. Each lane reads 16-byte
-// aligned vectors of col / val (aligned down from the row start, masked to
-// the row), gathers x, and the eight partial sums meet by shuffles.
+// Four lanes per row, eight rows per warp step. Each lane takes two 16-byte
+// aligned vectors of col / val per round (aligned down from the row start;
+// elements outside the row are masked), issues both loads before any x
+// gather, and the four partial sums meet by shuffles. Latency, not
+// bandwidth, limits a CSR row walk, so the kernel runs at full occupancy
+// and keeps 8 loads plus 8 gathers in flight per lane.
+template <typename Idx>
+__device__ __forceinline__ void spmv_vec(const int32_t* __restrict__ col, const float* __restrict__ val,
+                                         Idx v, Idx nnz4, Idx e1, int4& c, float4& w) {
+  if (v < nnz4) {
+    c = __ldcs(reinterpret_cast<const int4*>(col + v));
+    w = __ldcs(reinterpret_cast<const float4*>(val + v));
+  } else {  // last partial vector of the arrays: element loads inside [0, e1)
+    c = make_int4(0, 0, 0, 0);
+    w = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (v < e1) { c.x = col[v]; w.x = val[v]; }
+    if (v + 1 < e1) { c.y = col[v + 1]; w.y = val[v + 1]; }
+    if (v + 2 < e1) { c.z = col[v + 2]; w.z = val[v + 2]; }
+    if (v + 3 < e1) { c.w = col[v + 3]; w.w = val[v + 3]; }
+  }
+}
+
+template <typename Idx>
+__device__ __forceinline__ float spmv_fma4(const float* __restrict__ x, Idx v, Idx e0, Idx e1,
+                                           const int4& c, const float4& w, float acc) {
+  if (v >= e0 && v < e1) acc = fmaf(w.x, __ldg(x + c.x), acc);
+  if (v + 1 >= e0 && v + 1 < e1) acc = fmaf(w.y, __ldg(x + c.y), acc);
+  if (v + 2 >= e0 && v + 2 < e1) acc = fmaf(w.z, __ldg(x + c.z), acc);
+  if (v + 3 >= e0 && v + 3 < e1) acc = fmaf(w.w, __ldg(x + c.w), acc);
+  return acc;
+}
+
+// PtrT (int32 or int64 row_ptr) is also the element index type
 template <typename PtrT>
-__global__ void __launch_bounds__(kThreads) k_spmv(const PtrT* __restrict__ row_ptr,
-                                                   const int32_t* __restrict__ col,
-                                                   const float* __restrict__ val,
-                                                   const float* __restrict__ x, float* __restrict__ y,
-                                                   uint64_t rows, int vec, RelHook hook) {
+__global__ void __launch_bounds__(kThreads, 6) k_spmv(const PtrT* __restrict__ row_ptr,
+                                                      const int32_t* __restrict__ col,
+                                                      const float* __restrict__ val,
+                                                      const float* __restrict__ x, float* __restrict__ y,
+                                                      uint64_t rows, int vec, RelHook hook) {
+  using Idx = PtrT;
   const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t sub = lane & 7u;
+  const uint32_t sub = lane & 3u;
   const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t nnz = (int64_t)row_ptr[rows];
-  const int64_t nnz4 = nnz & ~(int64_t)3;  // vectors wholly inside the arrays
-  for (uint64_t rb = warp * 4; rb < rows; rb += nwarps * 4) {
-    const uint64_t r = rb + (lane >> 3);
-    int64_t e0 = 0, e1 = 0;
+  const Idx nnz = row_ptr[rows];
+  const Idx nnz4 = nnz & ~(Idx)3;  // vectors wholly inside the arrays
+  for (uint64_t rb = warp * 8; rb < rows; rb += nwarps * 8) {
+    const uint64_t r = rb + (lane >> 2);
+    Idx e0 = 0, e1 = 0;
     if (r < rows) {
-      e0 = (int64_t)row_ptr[r];
-      e1 = (int64_t)row_ptr[r + 1];
+      e0 = row_ptr[r];
+      e1 = row_ptr[r + 1];
     }
     float acc = 0.f;
     if (vec) {
-      for (int64_t v = (e0 & ~(int64_t)3) + 4 * (int64_t)sub; v < e1; v += 32) {
-        if (v < nnz4) {
-          int4 c4 = __ldcs(reinterpret_cast<const int4*>(col + v));
-          float4 w4 = __ldcs(reinterpret_cast<const float4*>(val + v));
-          if (v >= e0) acc = fmaf(w4.x, __ldg(x + c4.x), acc);
-          if (v + 1 >= e0 && v + 1 < e1) acc = fmaf(w4.y, __ldg(x + c4.y), acc);
-          if (v + 2 >= e0 && v + 2 < e1) acc = fmaf(w4.z, __ldg(x + c4.z), acc);
-          if (v + 3 >= e0 && v + 3 < e1) acc = fmaf(w4.w, __ldg(x + c4.w), acc);
-        } else {
-          for (int64_t e = v; e < v + 4 && e < e1; e++)
-            if (e >= e0) acc = fmaf(val[e], __ldg(x + col[e]), acc);
-        }
+      for (Idx v = (e0 & ~(Idx)3) + 4 * (Idx)sub; v < e1; v += 32) {
+        const Idx u = v + 16;
+        int4 ca, cb = make_int4(0, 0, 0, 0);
+        float4 wa, wb = make_float4(0.f, 0.f, 0.f, 0.f);
+        spmv_vec<Idx>(col, val, v, nnz4, e1, ca, wa);
+        if (u < e1) spmv_vec<Idx>(col, val, u, nnz4, e1, cb, wb);
+        acc = spmv_fma4<Idx>(x, v, e0, e1, ca, wa, acc);
+        if (u < e1) acc = spmv_fma4<Idx>(x, u, e0, e1, cb, wb, acc);
       }
     } else {
-      for (int64_t e = e0 + sub; e < e1; e += 8) acc = fmaf(val[e], __ldg(x + col[e]), acc);
+      for (Idx e = e0 + (Idx)sub; e < e1; e += 4) acc = fmaf(val[e], __ldg(x + col[e]), acc);
     }
-    acc += __shfl_xor_sync(SG_FULL, acc, 4);
     acc += __shfl_xor_sync(SG_FULL, acc, 2);
     acc += __shfl_xor_sync(SG_FULL, acc, 1);
     if (sub == 0 && r < rows) y[r] = acc;
@@ -254,7 +284,10 @@ __global__ void __launch_bounds__(kThreads) k_spmv_row_ptr(const uint64_t* __res
   }
 }
 
-// columns, values (index e < generated count, at most the capacity) and x
+// columns, values (index e < generated count, at most the capacity) and x.
+// Non-zeros come in pairs sharing one hash per quantity: the column pair
+// takes the high / low 32 bits, the value pair Box-Muller's cos / sin.
+// A thread writes four non-zeros (two pairs) with 16-byte stores.
 __global__ void __launch_bounds__(kThreads) k_spmv_fill(int32_t* __restrict__ col, float* __restrict__ val,
                                                         float* __restrict__ x, const uint64_t* total,
                                                         uint64_t cap, uint64_t rows, uint64_t kc,
@@ -262,9 +295,21 @@ __global__ void __launch_bounds__(kThreads) k_spmv_fill(int32_t* __restrict__ co
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t nnz = *total < cap ? *total : cap;
-  for (uint64_t e = tid; e < nnz; e += stride) {
-    col[e] = (int32_t)column_of(sm64_at(kc, e), rows);
-    val[e] = normal01(sm64_at(kv, e));
+  const uint64_t nq = nnz >> 2;
+  for (uint64_t q = tid; q < nq; q += stride) {
+    const uint64_t m = q << 1;
+    const uint64_t hc0 = sm64_at(kc, m), hc1 = sm64_at(kc, m + 1);
+    const int4 c = make_int4((int)column_of32((uint32_t)(hc0 >> 32), rows), (int)column_of32((uint32_t)hc0, rows),
+                             (int)column_of32((uint32_t)(hc1 >> 32), rows), (int)column_of32((uint32_t)hc1, rows));
+    const float2 v0 = normal_pair(sm64_at(kv, m)), v1 = normal_pair(sm64_at(kv, m + 1));
+    reinterpret_cast<int4*>(col)[q] = c;
+    reinterpret_cast<float4*>(val)[q] = make_float4(v0.x, v0.y, v1.x, v1.y);
+  }
+  for (uint64_t e = (nq << 2) + tid; e < nnz; e += stride) {
+    const uint64_t hc = sm64_at(kc, e >> 1);
+    col[e] = (int32_t)column_of32((e & 1) ? (uint32_t)hc : (uint32_t)(hc >> 32), rows);
+    const float2 v = normal_pair(sm64_at(kv, e >> 1));
+    val[e] = (e & 1) ? v.y : v.x;
   }
   for (uint64_t r = tid; r < rows; r += stride) x[r] = uniform_pm1(sm64_at(kx, r));
 }
@@ -309,13 +354,13 @@ static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 int launch_triad(float* a, const float* b, const float* c, float s, uint64_t n, const RelHook& h,
                  cudaStream_t st) {
   int vec = aligned16(a) && aligned16(b) && aligned16(c);
-  k_triad<<<grid_for((n + 7) / 8, kThreads), kThreads, 0, st>>>(a, b, c, s, n, vec, h);
+  k_triad<<<grid_for(n / 4 + 1, kThreads * 4), kThreads, 0, st>>>(a, b, c, s, n, vec, h);
   return cudaPeekAtLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
 }
 
 int launch_gen_triad(float* b, float* c, uint64_t n, uint64_t key, cudaStream_t st) {
   int vec = aligned16(b) && aligned16(c);
-  k_gen_triad<<<grid_for((n + 3) / 4, kThreads), kThreads, 0, st>>>(b, c, n, stream_key(key, 1),
+  k_gen_triad<<<grid_for(n / 4 + 1, kThreads * 4), kThreads, 0, st>>>(b, c, n, stream_key(key, 1),
                                                                      stream_key(key, 2), vec);
   return cudaPeekAtLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
 }
@@ -323,7 +368,7 @@ int launch_gen_triad(float* b, float* c, uint64_t n, uint64_t key, cudaStream_t 
 int launch_spmv(const void* row_ptr, int ptr64, const int32_t* col, const float* val, const float* x,
                 float* y, uint64_t rows, const RelHook& h, cudaStream_t st) {
   int vec = aligned16(col) && aligned16(val);
-  unsigned grid = grid_for((rows + 3) / 4, kThreads / 32);
+  unsigned grid = grid_for((rows + 7) / 8, (kThreads / 32) * 4);
   if (ptr64)
     k_spmv<int64_t><<<grid, kThreads, 0, st>>>((const int64_t*)row_ptr, col, val, x, y, rows, vec, h);
   else
@@ -363,7 +408,7 @@ int launch_gen_spmv(char* base, uint64_t rows, uint64_t nnz, const uint64_t* tab
   else
     k_spmv_row_ptr<int32_t><<<nch, kThreads, 0, st>>>(table, lk, rows, scan, L.nchunks,
                                                       (int32_t*)(base + L.row_ptr), nnz, err);
-  k_spmv_fill<<<grid_for(nnz > rows ? nnz : rows, kThreads * 4), kThreads, 0, st>>>(
+  k_spmv_fill<<<grid_for((nnz / 4 > rows ? nnz / 4 : rows), kThreads * 4), kThreads, 0, st>>>(
       (int32_t*)(base + L.col), (float*)(base + L.val), (float*)(base + L.x), scan + L.nchunks, nnz,
       rows, stream_key(key, 2), stream_key(key, 3), stream_key(key, 4));
   if (launches) *launches += 4;
@@ -372,12 +417,12 @@ int launch_gen_spmv(char* base, uint64_t rows, uint64_t nnz, const uint64_t* tab
 
 int launch_gen_bf16(uint16_t* out, uint64_t count, uint64_t key, cudaStream_t st) {
   if (!aligned16(out)) return SG_ERR_INVALID;
-  k_gen_bf16<<<grid_for((count + 7) / 8, kThreads * 2), kThreads, 0, st>>>(out, count, key);
+  k_gen_bf16<<<grid_for((count + 7) / 8, kThreads * 4), kThreads, 0, st>>>(out, count, key);
   return cudaPeekAtLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
 }
 
 int launch_digest(const void* p, uint64_t words, uint64_t* out, const RelHook& h, cudaStream_t st) {
-  k_digest<<<grid_for(words, kThreads * 8), kThreads, 0, st>>>((const uint32_t*)p, words, out, h);
+  k_digest<<<grid_for(words, kThreads * 16), kThreads, 0, st>>>((const uint32_t*)p, words, out, h);
   return cudaPeekAtLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
 }
 

@@ -1,0 +1,81 @@
+"""Run one job kernel on its own, for profiling and timing.
+
+    python -m paper_1712_04495_b300.kernel_cases gemm  [M=N=K, default 8192] [launches]
+    python -m paper_1712_04495_b300.kernel_cases spmv  [rows, default 1e7]   [launches]
+    python -m paper_1712_04495_b300.kernel_cases triad [n, default 64M]      [launches]
+    python -m paper_1712_04495_b300.kernel_cases fill  [rows, default 1e7]   [launches]
+
+The inputs are built by the library's own generators first (one launch per
+generator kernel), then the kernel runs `launches` times (default 3) on the
+current stream. Prints the CUDA-event time per launch.
+"""
+from __future__ import annotations
+
+import sys
+
+import numpy as np
+import torch
+
+from . import abi
+from . import tracegen as tg
+
+
+def _time(fn, launches: int) -> float:
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(launches):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / launches
+
+
+def run(kind: str, size: int | None = None, launches: int = 3) -> dict:
+    st = torch.cuda.current_stream().cuda_stream
+    if kind == "gemm":
+        m = size or 8192
+        A = torch.empty(m * m, dtype=torch.int16, device="cuda")
+        B = torch.empty(m * m, dtype=torch.int16, device="cuda")
+        C = torch.empty(m * m, dtype=torch.float32, device="cuda")
+        assert abi.sg_gen_gemm(A.data_ptr(), B.data_ptr(), m, m, m, 42, st) == 0
+        ms = _time(lambda: abi.sg_gemm_bf16(A.data_ptr(), B.data_ptr(), C.data_ptr(), m, m, m, st), launches)
+        return {"kernel": "gemm", "size": m, "ms": ms, "tflops": 2.0 * m ** 3 / (ms * 1e-3) / 1e12}
+    if kind in ("spmv", "fill"):
+        rows = size or 10_000_000
+        lam = 16.0
+        cap = tg.spmv_nnz_cap(rows, lam)
+        lay = tg.spmv_layout(rows, cap)
+        base = torch.empty(lay["total"], dtype=torch.uint8, device="cuda")
+        tab = torch.from_numpy(tg.poisson_cdf_table(lam).view(np.int64).copy()).cuda()
+        p = base.data_ptr()
+        gen = lambda: abi.sg_gen_spmv(p, rows, cap, tab.data_ptr(), 5, 0, st)  # noqa: E731
+        gen()
+        torch.cuda.synchronize()
+        if kind == "fill":
+            ms = _time(gen, launches)
+            return {"kernel": "spmv generator", "rows": rows, "ms": ms}
+        ptr_t = torch.int64 if lay["ptr64"] else torch.int32
+        esz = 8 if lay["ptr64"] else 4
+        nnz = int(base[lay["row_ptr"] + esz * rows:lay["row_ptr"] + esz * (rows + 1)].view(ptr_t).item())
+        ms = _time(lambda: abi.sg_spmv(p + lay["row_ptr"], lay["ptr64"], p + lay["col"], p + lay["val"],
+                                       p + lay["x"], p + lay["y"], rows, st), launches)
+        alg = esz * (rows + 1) + 8 * nnz + 8 * rows
+        return {"kernel": "spmv", "rows": rows, "nnz": nnz, "ms": ms, "alg_bytes": alg,
+                "gbs": alg / (ms * 1e-3) / 1e9}
+    if kind == "triad":
+        n = size or (64 << 20)
+        buf = torch.empty(3 * n, dtype=torch.float32, device="cuda")
+        a, b, c = buf[:n], buf[n:2 * n], buf[2 * n:]
+        assert abi.sg_gen_triad(b.data_ptr(), c.data_ptr(), n, 7, st) == 0
+        ms = _time(lambda: abi.sg_triad(a.data_ptr(), b.data_ptr(), c.data_ptr(), 3.0, n, st), launches)
+        return {"kernel": "triad", "n": n, "ms": ms, "gbs": 12.0 * n / (ms * 1e-3) / 1e9}
+    raise ValueError(kind)
+
+
+if __name__ == "__main__":
+    k = sys.argv[1]
+    size = int(float(sys.argv[2])) if len(sys.argv) > 2 else None
+    launches = int(sys.argv[3]) if len(sys.argv) > 3 else 3
+    print(run(k, size, launches))

@@ -19,15 +19,20 @@ its data stream ``s`` has key ``K_{j,s} = out(K_j, s)``; element ``i`` of that
 stream is drawn from ``h = out(K_{j,s}, i)``.
 
   uniform[-1, 1)  u = (h >> 40) * 2^-23 - 1                 (exact in fp32)
-  normal(0, 1)    u1 = ((h >> 40) + 1) * 2^-24,  u2 = ((h >> 16) & 0xFFFFFF) * 2^-24,
-                  v = sqrt(-2 ln u1) * cos(2 pi u2)          (Box-Muller)
-  column in [0,n) c = ((h >> 32) * n) >> 32                  (multiply-shift)
   row length      L = #{k : T[k] <= (h >> 32)}, T the Poisson CDF table below
   bf16            round-to-nearest-even of the fp32 uniform
 
+SpMV non-zeros come in pairs (e = 2m, 2m + 1), one hash per pair and per
+quantity, h = out(K, m):
+  column in [0,n) c = (w * n) >> 32 with w = h >> 32 for e even, h & 0xFFFFFFFF
+                  for e odd (multiply-shift)
+  value N(0,1)    u1 = ((h >> 40) + 1) * 2^-24, u2 = ((h >> 16) & 0xFFFFFF) * 2^-24,
+                  r = sqrt(-2 ln u1); v = r cos(2 pi u2) for e even, r sin(2 pi u2)
+                  for e odd (Box-Muller's two independent normals)
+
 Streams: triad b=1, c=2; GEMM A=1 (index i*K+k), B^T=2 (index j*K+k);
-SpMV row lengths=1 (index row), columns=2 (index e), values=3 (index e),
-x=4 (index col).
+SpMV row lengths=1 (index row), columns=2 (index e // 2), values=3 (index
+e // 2), x=4 (index col).
 
 Job record (``JOB_DTYPE``, 64 bytes, the C struct ``sg_job``): arrival,
 declared bytes, declared duration (replay clock), timeout, data key, kind
@@ -103,17 +108,32 @@ def uniform_pm1_f32(h) -> np.ndarray:
     return ((h >> _U64(40)).astype(np.float64) * 2.0 ** -23 - 1.0).astype(np.float32)
 
 
-def normal_f32(h) -> np.ndarray:
+def normal_pair_f32(h, odd) -> np.ndarray:
+    """Box-Muller: the cos branch for even elements, the sin branch for odd."""
     h = np.asarray(h, dtype=_U64)
     u1 = ((h >> _U64(40)).astype(np.float64) + 1.0) * 2.0 ** -24
     u2 = ((h >> _U64(16)) & _U64(0xFFFFFF)).astype(np.float64) * 2.0 ** -24
-    return (np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)).astype(np.float32)
+    r = np.sqrt(-2.0 * np.log(u1))
+    ang = 2.0 * np.pi * u2
+    return np.where(np.asarray(odd, bool), r * np.sin(ang), r * np.cos(ang)).astype(np.float32)
 
 
-def column_index(h, n: int) -> np.ndarray:
+def column_pair(h, odd, n: int) -> np.ndarray:
+    """Multiply-shift of the high (even element) or low (odd) 32 bits."""
     h = np.asarray(h, dtype=_U64)
+    w = np.where(np.asarray(odd, bool), h & _U64(0xFFFFFFFF), h >> _U64(32))
     with np.errstate(over="ignore"):
-        return (((h >> _U64(32)) * _U64(n)) >> _U64(32)).astype(np.int64)
+        return ((w * _U64(n)) >> _U64(32)).astype(np.int64)
+
+
+def spmv_columns(col_key: int, e, n: int) -> np.ndarray:
+    e = np.asarray(e, dtype=_U64)
+    return column_pair(sm64_at(col_key, e >> _U64(1)), (e & _U64(1)) == _U64(1), n)
+
+
+def spmv_values(val_key: int, e) -> np.ndarray:
+    e = np.asarray(e, dtype=_U64)
+    return normal_pair_f32(sm64_at(val_key, e >> _U64(1)), (e & _U64(1)) == _U64(1))
 
 
 def bf16_bits_rne(x_f32) -> np.ndarray:

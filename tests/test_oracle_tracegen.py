@@ -74,17 +74,28 @@ def test_row_length_statistics():
     assert abs(lens.var() - 16.0) < 0.3
 
 
-def test_columns_in_range():
-    h = tg.sm64_at(3, np.arange(100000))
+def test_columns_in_range_and_uniform():
+    e = np.arange(200000)
     for n in (1, 7, 1000, 10_000_000):
-        c = tg.column_index(h, n)
+        c = tg.spmv_columns(3, e, n)
         assert c.min() >= 0 and c.max() < n
+    c = tg.spmv_columns(3, e, 10)
+    counts = np.bincount(c, minlength=10)
+    assert np.all(np.abs(counts - 20000) < 5 * np.sqrt(20000))
+    # an even and an odd element share a hash but use different halves
+    assert np.mean(tg.spmv_columns(3, e[0::2], 1 << 20) == tg.spmv_columns(3, e[1::2], 1 << 20)) < 1e-3
 
 
-def test_normal_moments():
-    v = tg.normal_f32(tg.sm64_at(5, np.arange(400000))).astype(np.float64)
+def test_normal_pair_moments_and_independence():
+    v = tg.spmv_values(5, np.arange(400000)).astype(np.float64)
     assert abs(v.mean()) < 0.01 and abs(v.std() - 1.0) < 0.01
     assert np.all(np.isfinite(v))
+    even, odd = v[0::2], v[1::2]
+    assert abs(np.corrcoef(even, odd)[0, 1]) < 0.01
+    # the pair lies on one circle: even^2 + odd^2 = -2 ln u1
+    h = tg.sm64_at(5, np.arange(200000))
+    u1 = ((h >> np.uint64(40)).astype(np.float64) + 1.0) * 2.0 ** -24
+    assert np.allclose(even ** 2 + odd ** 2, -2.0 * np.log(u1), rtol=1e-5, atol=1e-5)
 
 
 def test_layouts_aligned():
