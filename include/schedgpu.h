@@ -259,10 +259,20 @@ int sg_gen_spmv(void* base, uint64_t rows, uint64_t nnz_cap, const uint64_t* tab
 
 /* BF16 GEMM on tcgen05 tensor cores: C[M x N] (fp32, row-major) =
  * A[M x K] (bf16, row-major) * B, with B given transposed as Bt[N x K]
- * (bf16, row-major, K contiguous). M and N multiples of 128, K a multiple
- * of 64 (else SG_ERR_INVALID); pointers 16-byte aligned. */
+ * (bf16, row-major, K contiguous). Any M, N; K a positive multiple of 8
+ * (rows of A and Bt must start on 16-byte boundaries), else
+ * SG_ERR_INVALID; pointers 16-byte aligned. Ragged tiles are zero-filled
+ * by TMA and masked on store. */
 int sg_gemm_bf16(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, uint32_t N,
                  uint32_t K, void* stream);
+
+/* sg_gemm_bf16 with an explicit output-tile width: tile_n = 64, 128 or 256
+ * columns per 128-row tile (0 = the built-in choice, sg_gemm_tile_n). */
+int sg_gemm_bf16_tiled(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, uint32_t N,
+                       uint32_t K, uint32_t tile_n, void* stream);
+/* The tile width sg_gemm_bf16 picks for an M x N output: the widest that
+ * still gives every SM a tile with at most 1/8 of it wasted. Host only. */
+uint32_t sg_gemm_tile_n(uint32_t M, uint32_t N);
 
 /* GEMM inputs: A[i,k] = bf16(U(stream 1, i*K+k)), Bt[j,k] = bf16(U(stream 2, j*K+k)). */
 int sg_gen_gemm(uint16_t* A, uint16_t* Bt, uint32_t M, uint32_t N, uint32_t K, uint64_t key,

@@ -86,6 +86,8 @@ _SIGS = {
     "sg_spmv": ([_P, ctypes.c_int, _P, _P, _P, _P, _U64, _P], ctypes.c_int),
     "sg_gen_spmv": ([_P, _U64, _U64, _P, _U64, _P, _P], ctypes.c_int),
     "sg_gemm_bf16": ([_P, _P, _P, _U32, _U32, _U32, _P], ctypes.c_int),
+    "sg_gemm_bf16_tiled": ([_P, _P, _P, _U32, _U32, _U32, _U32, _P], ctypes.c_int),
+    "sg_gemm_tile_n": ([_U32, _U32], _U32),
     "sg_gen_gemm": ([_P, _P, _U32, _U32, _U32, _U64, _P], ctypes.c_int),
     "sg_digest": ([_P, _U64, _P, _P], ctypes.c_int),
 }
@@ -227,6 +229,14 @@ def sg_gen_spmv(base, rows: int, nnz: int, table_ptr, key: int, err_ptr=0, strea
 
 def sg_gemm_bf16(A, Bt, C, M: int, N: int, K: int, stream: int = 0) -> int:
     return lib().sg_gemm_bf16(A, Bt, C, M, N, K, stream)
+
+
+def sg_gemm_bf16_tiled(A, Bt, C, M: int, N: int, K: int, tile_n: int, stream: int = 0) -> int:
+    return lib().sg_gemm_bf16_tiled(A, Bt, C, M, N, K, tile_n, stream)
+
+
+def sg_gemm_tile_n(M: int, N: int) -> int:
+    return lib().sg_gemm_tile_n(M, N)
 
 
 def sg_gen_gemm(A, Bt, M: int, N: int, K: int, key: int, stream: int = 0) -> int:

@@ -170,7 +170,9 @@ __global__ void __launch_bounds__(kThreadsG, 1)
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t ring = (raw + 1023u) & ~1023u;
 
-  const uint32_t mt = M / kBM, nt = N / BN, kb_n = K / kBK;
+  // ragged edges: TMA fills rows / columns outside the tensors with zeros,
+  // the epilogue masks rows >= M and columns >= N
+  const uint32_t mt = (M + kBM - 1) / kBM, nt = (N + BN - 1) / BN, kb_n = (K + kBK - 1) / kBK;
   const uint32_t tiles = mt * nt;
 
   if (threadIdx.x == 0) {
@@ -267,16 +269,26 @@ __global__ void __launch_bounds__(kThreadsG, 1)
       if (!__all_sync(SG_FULL, ok)) break;
       tc_fence_after();
       const uint32_t row = m * kBM + q * 32 + lane;
-      float* crow = C + (uint64_t)row * N + (uint64_t)n * BN;
+      const uint32_t col0 = n * BN;
+      float* crow = C + (uint64_t)row * N + col0;
+      const bool vec_ok = (N & 3u) == 0;
 #pragma unroll 1
       for (uint32_t c = 0; c < BN / 32; c++) {
+        if (col0 + c * 32 >= N) break;             // warp-uniform
         uint32_t r[32];
         tmem_ld_32cols(tmem + ((q * 32u) << 16) + acc * BN + c * 32, r);
-        float4* dst = reinterpret_cast<float4*>(crow + c * 32);
+        if (row >= M) continue;
+        if (vec_ok && col0 + c * 32 + 32 <= N) {
+          float4* dst = reinterpret_cast<float4*>(crow + c * 32);
 #pragma unroll
-        for (int v = 0; v < 8; v++)
-          dst[v] = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
-                               __uint_as_float(r[4 * v + 2]), __uint_as_float(r[4 * v + 3]));
+          for (int v = 0; v < 8; v++)
+            dst[v] = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
+                                 __uint_as_float(r[4 * v + 2]), __uint_as_float(r[4 * v + 3]));
+        } else {
+#pragma unroll
+          for (int v = 0; v < 32; v++)
+            if (col0 + c * 32 + v < N) crow[c * 32 + v] = __uint_as_float(r[v]);
+        }
       }
       tc_fence_before();
       mbar_arrive(smem_u32(&bar_acc_empty[acc]));
@@ -334,7 +346,7 @@ int launch_bn(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, uint3
   if (attr_rc != cudaSuccess) return SG_ERR_CUDA;
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, M, K, kBM) || !make_map(&mb, Bt, N, K, BN)) return SG_ERR_CUDA;
-  uint32_t tiles = (M / kBM) * (N / BN);
+  uint32_t tiles = ((M + kBM - 1) / kBM) * ((N + BN - 1) / BN);
   uint32_t grid = tiles < (uint32_t)num_sms() ? tiles : (uint32_t)num_sms();
   k_gemm_tc<BN><<<grid, kThreadsG, smem, st>>>(ma, mb, C, M, N, K, h);
   return cudaPeekAtLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
@@ -342,13 +354,37 @@ int launch_bn(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, uint3
 
 }  // namespace
 
-int launch_gemm(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, uint32_t N, uint32_t K,
-                const RelHook& h, cudaStream_t st) {
-  if (M == 0 || N == 0 || K == 0 || M % kBM || N % 128 || K % kBK) return SG_ERR_INVALID;
+// Output-tile width: the widest of 256 / 128 / 64 that still gives every SM
+// at least one tile with at most 1/8 of the width wasted on the ragged
+// edge; small GEMMs are latency-bound and take the narrowest (most tiles).
+int gemm_pick_bn(uint32_t M, uint32_t N) {
+  const uint32_t mt = (M + kBM - 1) / kBM;
+  const uint32_t sms = (uint32_t)num_sms();
+  for (uint32_t bn : {256u, 128u}) {
+    if (N < bn) continue;
+    const uint32_t nt = (N + bn - 1) / bn;
+    const bool waste_ok = (nt * bn - N) * 8 <= N;
+    if (waste_ok && mt * nt >= sms) return (int)bn;
+  }
+  return 64;
+}
+
+int launch_gemm_bn(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, uint32_t N, uint32_t K,
+                   int bn, const RelHook& h, cudaStream_t st) {
+  if (M == 0 || N == 0) return SG_OK;
+  if (K == 0 || K % 8) return SG_ERR_INVALID;       // TMA row stride: a multiple of 16 bytes
   if (((uintptr_t)A & 15) || ((uintptr_t)Bt & 15) || ((uintptr_t)C & 15)) return SG_ERR_INVALID;
   if (!encode_fn()) return SG_ERR_CUDA;
-  if (N % 256 == 0) return launch_bn<256>(A, Bt, C, M, N, K, h, st);
-  return launch_bn<128>(A, Bt, C, M, N, K, h, st);
+  if (bn <= 0) bn = gemm_pick_bn(M, N);
+  if (bn == 256) return launch_bn<256>(A, Bt, C, M, N, K, h, st);
+  if (bn == 128) return launch_bn<128>(A, Bt, C, M, N, K, h, st);
+  if (bn == 64) return launch_bn<64>(A, Bt, C, M, N, K, h, st);
+  return SG_ERR_INVALID;
+}
+
+int launch_gemm(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, uint32_t N, uint32_t K,
+                const RelHook& h, cudaStream_t st) {
+  return launch_gemm_bn(A, Bt, C, M, N, K, 0, h, st);
 }
 
 }  // namespace sg
@@ -360,6 +396,17 @@ extern "C" int sg_gemm_bf16(const uint16_t* A, const uint16_t* Bt, float* C, uin
   memset(&h, 0, sizeof h);
   return sg::launch_gemm(A, Bt, C, M, N, K, h, (cudaStream_t)stream);
 }
+
+extern "C" int sg_gemm_bf16_tiled(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, uint32_t N,
+                                  uint32_t K, uint32_t tile_n, void* stream) {
+  if (!A || !Bt || !C) return SG_ERR_INVALID;
+  if (tile_n != 0 && tile_n != 64 && tile_n != 128 && tile_n != 256) return SG_ERR_INVALID;
+  sg::RelHook h;
+  memset(&h, 0, sizeof h);
+  return sg::launch_gemm_bn(A, Bt, C, M, N, K, (int)tile_n, h, (cudaStream_t)stream);
+}
+
+extern "C" uint32_t sg_gemm_tile_n(uint32_t M, uint32_t N) { return (uint32_t)sg::gemm_pick_bn(M, N); }
 
 extern "C" int sg_kernel_errors(uint32_t* flags_out) {
   if (!flags_out) return SG_ERR_INVALID;

@@ -31,6 +31,10 @@ int launch_digest(const void* p, uint64_t words, uint64_t* out, const RelHook& h
 // tcgen05 GEMM (gemm.cu): C = A * Bt^T
 int launch_gemm(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, uint32_t N, uint32_t K,
                 const RelHook& h, cudaStream_t st);
+// the same with an explicit output-tile width (64, 128 or 256; 0 = heuristic)
+int launch_gemm_bn(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, uint32_t N, uint32_t K,
+                   int bn, const RelHook& h, cudaStream_t st);
+int gemm_pick_bn(uint32_t M, uint32_t N);
 
 // generator + kernel (+ digest when keep_slot) of one job inside its grant
 int launch_job(const sg_job& job, char* base, const uint64_t* tables, const RelHook& hook,

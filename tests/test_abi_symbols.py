@@ -52,5 +52,5 @@ def test_host_only_calls(lib):
     assert lib.sg_replay_workspace_bytes(1000) > 1000 * 48
     # argument checks happen before any device work
     assert lib.sg_init(None, None, ctypes.c_uint64(0), None) == 4
-    assert lib.sg_gemm_bf16(ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), 100, 128, 64,
+    assert lib.sg_gemm_bf16(ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), 100, 128, 63,
                             None) == 4

@@ -104,20 +104,25 @@ def test_spmv_full_size_sampled():
     assert np.all(np.abs(gy - y) <= 1e-5 * mag + 1e-30)
 
 
-def _gemm(M, N, Kd, key):
+def _gemm(M, N, Kd, key, tile_n=None):
     abi = _abi()
     A = torch.empty(M * Kd, dtype=torch.int16, device="cuda")
     Bt = torch.empty(N * Kd, dtype=torch.int16, device="cuda")
     C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
     assert abi.sg_gen_gemm(A.data_ptr(), Bt.data_ptr(), M, N, Kd, key) == 0
-    assert abi.sg_gemm_bf16(A.data_ptr(), Bt.data_ptr(), C.data_ptr(), M, N, Kd) == 0
+    if tile_n is None:
+        assert abi.sg_gemm_bf16(A.data_ptr(), Bt.data_ptr(), C.data_ptr(), M, N, Kd) == 0
+    else:
+        assert abi.sg_gemm_bf16_tiled(A.data_ptr(), Bt.data_ptr(), C.data_ptr(), M, N, Kd, tile_n) == 0
     torch.cuda.synchronize()
     assert abi.sg_kernel_errors() == 0
     return A, Bt, C
 
 
 @pytest.mark.parametrize("M,N,Kd", [(128, 128, 64), (128, 256, 128), (256, 384, 192),
-                                    (512, 512, 512), (1024, 1024, 1024), (384, 640, 2048)])
+                                    (512, 512, 512), (1024, 1024, 1024), (384, 640, 2048),
+                                    (64, 64, 64), (1, 1, 8), (200, 72, 40), (129, 257, 520),
+                                    (300, 1000, 8), (4096, 4096, 256)])
 def test_gemm_matches_fp64(M, N, Kd):
     key = 1234 + M + N + Kd
     A, Bt, C = _gemm(M, N, Kd, key)
@@ -132,6 +137,24 @@ def test_gemm_matches_fp64(M, N, Kd):
     assert rel <= 2e-2
     # fp32 accumulation of exact bf16 products: error ~ sqrt(K) * 2^-24
     assert rel <= 1e-5, rel
+
+
+@pytest.mark.parametrize("tile_n", [64, 128, 256])
+@pytest.mark.parametrize("M,N,Kd", [(256, 512, 128), (300, 520, 136), (130, 70, 64)])
+def test_gemm_every_tile_width(M, N, Kd, tile_n):
+    key = 77 + M + N + Kd + tile_n
+    A, Bt, C = _gemm(M, N, Kd, key, tile_n)
+    ref = K.gemm(key, M, N, Kd)
+    got = C.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(got))
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-5
+
+
+def test_gemm_tile_choice():
+    abi = _abi()
+    assert abi.sg_gemm_tile_n(8192, 8192) == 256
+    assert abi.sg_gemm_tile_n(2048, 2048) == 128
+    assert abi.sg_gemm_tile_n(512, 512) == 64
 
 
 def test_gemm_full_size_sampled():
@@ -149,8 +172,10 @@ def test_gemm_full_size_sampled():
 
 def test_gemm_rejects_bad_shapes():
     abi = _abi()
-    assert abi.sg_gemm_bf16(16, 16, 16, 100, 128, 64) == abi.SG_ERR_INVALID
-    assert abi.sg_gemm_bf16(16, 16, 16, 128, 128, 63) == abi.SG_ERR_INVALID
+    assert abi.sg_gemm_bf16(16, 16, 16, 128, 128, 63) == abi.SG_ERR_INVALID   # K % 8
+    assert abi.sg_gemm_bf16(16, 16, 16, 128, 128, 0) == abi.SG_ERR_INVALID
+    assert abi.sg_gemm_bf16(24, 16, 16, 128, 128, 64) == abi.SG_ERR_INVALID   # misaligned A
+    assert abi.sg_gemm_bf16(16, 16, 16, 0, 128, 64) == abi.SG_OK              # empty: no work
 
 
 def test_digest_is_order_free_sum():
