@@ -207,7 +207,7 @@ int sg_replay(const sg_job* jobs_dev, uint32_t n, uint64_t budget, uint64_t gran
  * scheduler accounts for, and could fail or push a co-scheduled job out of
  * memory), and latency-critical host loops that must not enter the CUDA
  * allocator. The caller passes the jobs, the log and the stats as for
- * sg_replay; the workspace is a fixed array of 1600 KiB inside the
+ * sg_replay; the workspace is a fixed array of 2048 KiB inside the
  * library's device image, which every GPU that loads the library holds
  * until the process exits. Up to SG_REPLAY_NOALLOC_MAX_JOBS jobs; larger
  * traces get SG_ERR_TOO_LARGE and nothing runs. The first call on each
@@ -225,6 +225,46 @@ int sg_replay_noalloc(const sg_job* jobs_dev, uint32_t n, uint64_t budget, uint6
  * GEMM's mbarrier waits), OR-ed since the last call, then cleared.
  * Synchronous (device-wide). */
 int sg_kernel_errors(uint32_t* flags_out);
+
+/* ------------------------------------------------------- batching */
+/* One CUDA graph for a whole trace: a static co-schedule. plan (host, n
+ * records) is the log of sg_replay on the same jobs and pool size: it
+ * fixes each job's offset in the pool and the grant order. Every job
+ * becomes a child graph (its generators, its kernel, and with keep_dev its
+ * output digest into keep_dev[j]); a job depends on every job that used any
+ * byte of its extent earlier in grant order, so jobs that share memory
+ * never overlap in time and the others run concurrently. The graph owns no
+ * memory: dev_pool (pool_bytes) and tables_dev must outlive it. Build once,
+ * launch many times; keep_dev accumulates, so zero it before each launch.
+ * Jobs the plan did not grant are left out. */
+typedef struct sg_graph sg_graph;
+int sg_graph_build(void* dev_pool, uint64_t pool_bytes, const sg_job* jobs, uint32_t n,
+                   const uint64_t* tables_dev, const sg_record* plan, uint64_t* keep_dev,
+                   sg_graph** out);
+int sg_graph_launch(sg_graph* g, void* stream);
+int sg_graph_info(const sg_graph* g, uint64_t* jobs, uint64_t* kernels, uint64_t* edges);
+int sg_graph_destroy(sg_graph* g);
+
+/* The same plan run by one persistent grouped kernel: every job is a
+ * short program of phases (generators, kernel, optional digest), each
+ * phase a set of block-sized chunks; all blocks of one cooperative launch
+ * pull chunks from a single device work queue. A job's first chunks are
+ * queued when every earlier job that used any byte of its extent has
+ * finished, and the block finishing a phase queues the next one, so the
+ * batch runs with no host round trip and no launch per job. Arguments as
+ * for sg_graph_build; the object allocates its own device state (queue,
+ * dependency lists) once at build time, never at launch. GEMM jobs need
+ * K % 8 == 0. sg_batch_launch zeroes keep_dev itself. sg_batch_status
+ * (synchronous) reports finished jobs and error flags: SG_OK when every
+ * planned job finished, SG_ERR_DEVICE otherwise. */
+typedef struct sg_batch sg_batch;
+int sg_batch_build(void* dev_pool, uint64_t pool_bytes, const sg_job* jobs, uint32_t n,
+                   const uint64_t* tables_dev, const sg_record* plan, uint64_t* keep_dev,
+                   sg_batch** out);
+int sg_batch_launch(sg_batch* b, void* stream);
+int sg_batch_status(sg_batch* b, uint64_t* jobs_done, uint32_t* err_flags);
+int sg_batch_info(const sg_batch* b, uint64_t* jobs, uint64_t* chunks, uint64_t* blocks);
+int sg_batch_destroy(sg_batch* b);
 
 /* Engine error flags of the context (0 = none). */
 uint32_t sg_device_error(sg_ctx* ctx);

@@ -78,6 +78,15 @@ _SIGS = {
     "sg_replay_workspace_bytes": ([_U32], _U64),
     "sg_replay": ([_P, _U32, _U64, _U64, _U32, _U32, _U32, _P, _P, _P, _P], ctypes.c_int),
     "sg_replay_noalloc": ([_P, _U32, _U64, _U64, _U32, _U32, _U32, _P, _P, _P], ctypes.c_int),
+    "sg_graph_build": ([_P, _U64, _P, _U32, _P, _P, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "sg_graph_launch": ([_P, _P], ctypes.c_int),
+    "sg_graph_info": ([_P, ctypes.POINTER(_U64), ctypes.POINTER(_U64), ctypes.POINTER(_U64)], ctypes.c_int),
+    "sg_graph_destroy": ([_P], ctypes.c_int),
+    "sg_batch_build": ([_P, _U64, _P, _U32, _P, _P, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "sg_batch_launch": ([_P, _P], ctypes.c_int),
+    "sg_batch_status": ([_P, ctypes.POINTER(_U64), ctypes.POINTER(_U32)], ctypes.c_int),
+    "sg_batch_info": ([_P, ctypes.POINTER(_U64), ctypes.POINTER(_U64), ctypes.POINTER(_U64)], ctypes.c_int),
+    "sg_batch_destroy": ([_P], ctypes.c_int),
     "sg_kernel_errors": ([ctypes.POINTER(_U32)], ctypes.c_int),
     "sg_device_error": ([_P], _U32),
     "sg_strerror": ([ctypes.c_int], ctypes.c_char_p),
@@ -198,6 +207,60 @@ def sg_replay_noalloc(jobs_ptr: int, n: int, budget: int, granule: int, policy, 
     pol = POLICIES[policy] if isinstance(policy, str) else int(policy)
     return lib().sg_replay_noalloc(jobs_ptr, n, budget, granule, pol, flags, int(bool(exclusive)),
                                    log_ptr, stats_ptr or None, stream)
+
+
+def sg_graph_build(pool_ptr: int, pool_bytes: int, jobs: np.ndarray, tables_ptr: int, plan: np.ndarray,
+                   keep_ptr: int = 0) -> int:
+    jobs = np.ascontiguousarray(jobs, dtype=JOB_DTYPE)
+    plan = np.ascontiguousarray(plan, dtype=RECORD_DTYPE)
+    out = _P()
+    _check(lib().sg_graph_build(pool_ptr, pool_bytes, jobs.ctypes.data, len(jobs), tables_ptr or None,
+                                plan.ctypes.data, keep_ptr or None, ctypes.byref(out)), "sg_graph_build")
+    return out.value
+
+
+def sg_graph_launch(g: int, stream: int = 0) -> int:
+    return lib().sg_graph_launch(g, stream)
+
+
+def sg_graph_info(g: int):
+    a, b, c = _U64(), _U64(), _U64()
+    _check(lib().sg_graph_info(g, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "sg_graph_info")
+    return {"jobs": a.value, "kernels": b.value, "edges": c.value}
+
+
+def sg_graph_destroy(g: int):
+    _check(lib().sg_graph_destroy(g), "sg_graph_destroy")
+
+
+def sg_batch_build(pool_ptr: int, pool_bytes: int, jobs: np.ndarray, tables_ptr: int, plan: np.ndarray,
+                   keep_ptr: int = 0) -> int:
+    jobs = np.ascontiguousarray(jobs, dtype=JOB_DTYPE)
+    plan = np.ascontiguousarray(plan, dtype=RECORD_DTYPE)
+    out = _P()
+    _check(lib().sg_batch_build(pool_ptr, pool_bytes, jobs.ctypes.data, len(jobs), tables_ptr or None,
+                                plan.ctypes.data, keep_ptr or None, ctypes.byref(out)), "sg_batch_build")
+    return out.value
+
+
+def sg_batch_launch(b: int, stream: int = 0) -> int:
+    return lib().sg_batch_launch(b, stream)
+
+
+def sg_batch_status(b: int):
+    d, e = _U64(), _U32()
+    rc = lib().sg_batch_status(b, ctypes.byref(d), ctypes.byref(e))
+    return rc, d.value, e.value
+
+
+def sg_batch_info(b: int):
+    a, c, k = _U64(), _U64(), _U64()
+    _check(lib().sg_batch_info(b, ctypes.byref(a), ctypes.byref(c), ctypes.byref(k)), "sg_batch_info")
+    return {"jobs": a.value, "chunks": c.value, "blocks": k.value}
+
+
+def sg_batch_destroy(b: int):
+    _check(lib().sg_batch_destroy(b), "sg_batch_destroy")
 
 
 def sg_kernel_errors() -> int:

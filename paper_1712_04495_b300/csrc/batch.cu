@@ -1,0 +1,529 @@
+// Batching in one persistent grouped kernel.
+//
+// A batch of (typically thousands of tiny) jobs is admitted as a whole by the
+// device engine: sg_replay on the declared durations gives each job its
+// offset in the pool and its grant order (the plan). This kernel then runs
+// the plan as a dataflow. Every job is a short program of phases (input
+// generators, kernel, optional output digest); every phase is a set of
+// chunks, the per-block bodies shared with the standalone kernels
+// (tiles.cuh). Blocks pull chunks from one work queue; the block that
+// finishes the last chunk of a phase enqueues the next phase, and the block
+// that finishes a job makes each successor whose memory it was using one
+// step closer to runnable. A job's chunks are enqueued only when every
+// earlier job that used any byte of its extent has finished, so jobs that
+// share memory never overlap in time. There is no host round trip and no
+// launch per job.
+//
+// The work queue is a ring of exactly `total` slots (the chunk count of the
+// whole batch, known in advance): slot i is written once, and its sequence
+// word becomes i + 1 when the item is visible. A block claims the next slot
+// with one atomic and waits (bounded) until it is filled; a block that
+// claims a slot past the end has nothing left to do and leaves. All blocks
+// are co-resident (cooperative launch), so a waiting block never keeps the
+// producer of its slot from running.
+#include <vector>
+
+#include "engine.cuh"
+#include "jobs.h"
+#include "plan.h"
+#include "tc.cuh"
+#include "tiles.cuh"
+
+namespace sg {
+namespace {
+
+constexpr uint64_t kBatchWaitNs = 20000000000ull;  // 20 s for one queue slot
+constexpr uint32_t kBatchSmem = 50 * 1024;          // also caps residency at 4 blocks / SM
+constexpr uint32_t kBatchTmemCols = 128;            // 4 blocks x 128 = the SM's 512 columns
+constexpr uint32_t kGemmBM = 128;
+
+struct Item {
+  uint32_t job, phase;
+  uint64_t chunk;
+};
+
+struct BatchDev {
+  const sg_job* jobs;
+  const uint64_t* offset;        // [n] grant offsets (the plan)
+  char* pool;
+  const uint64_t* tables;
+  uint64_t* keep;                // [n] output digests, or null
+  const uint64_t* succ_ptr;      // [n + 1]
+  const uint32_t* succ;
+  uint32_t* dep;                 // [n] unfinished predecessors
+  uint32_t* left;                // [n] unfinished chunks of the current phase
+  Item* items;                   // [total]
+  uint32_t* seq;                 // [total]
+  unsigned long long* ctr;       // [0] head (claims), [1] tail (reservations), [2] jobs done
+  uint32_t* err;
+  uint64_t total;
+};
+
+__host__ __device__ inline uint32_t gemm_bn_small(uint64_t n) { return n > 64 ? 128u : 64u; }
+
+__host__ __device__ inline uint32_t job_phases(const sg_job& j, bool keep) {
+  const uint32_t p = j.kind == SG_KIND_SPMV ? 4u : 2u;
+  return p + (keep ? 1u : 0u);
+}
+
+__host__ __device__ inline uint64_t cdiv(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+
+// chunks of phase `ph` of job `j` (the digest phase comes last when kept)
+__host__ __device__ inline uint64_t phase_chunks(const sg_job& j, uint32_t ph) {
+  if (j.kind == SG_KIND_TRIAD) {
+    if (ph <= 1) return cdiv(j.p0, kTriadChunk);
+    return cdiv(j.p0, kDigestChunk);
+  }
+  if (j.kind == SG_KIND_GEMM) {
+    const uint64_t m = j.p0, n = j.p1, k = j.p2;
+    if (ph == 0) return cdiv(m * k, kBf16Chunk) + cdiv(n * k, kBf16Chunk);
+    if (ph == 1) return cdiv(m, kGemmBM) * cdiv(n, gemm_bn_small(n));
+    return cdiv(m * n, kDigestChunk);
+  }
+  const uint64_t rows = j.p0, cap = j.p1;
+  const uint64_t nch = cdiv(rows, kRowsPerScanChunk);
+  switch (ph) {
+    case 0: return nch + cdiv(cap > 4 * rows ? cap : 4 * rows, kFillChunk);
+    case 1: return 1;
+    case 2: return nch;
+    case 3: return cdiv(rows, kSpmvRowsChunk);
+    default: return cdiv(rows, kDigestChunk);
+  }
+}
+
+// ------------------------------------------------------------- queue ops
+// Called by one thread: reserve and publish the chunks of one phase.
+__device__ void push_phase(const BatchDev& B, uint32_t job, uint32_t ph) {
+  const uint64_t cnt = phase_chunks(B.jobs[job], ph);
+  stcg(B.left + job, (uint32_t)cnt);
+  __threadfence();
+  const uint64_t base = atomicAdd(&B.ctr[1], (unsigned long long)cnt);
+  if (base + cnt > B.total) {
+    atomicOr(B.err, ERR_CAP);
+    return;
+  }
+  for (uint64_t i = 0; i < cnt; i++) {
+    Item it;
+    it.job = job;
+    it.phase = ph;
+    it.chunk = i;
+    B.items[base + i] = it;
+  }
+  __threadfence();
+  for (uint64_t i = 0; i < cnt; i++) atomicExch(B.seq + base + i, (uint32_t)(base + i + 1));
+}
+
+// Claim the next slot; 1 = item in *out, 0 = nothing left, -1 = gave up.
+__device__ int pop(const BatchDev& B, Item* out) {
+  const uint64_t pos = atomicAdd(&B.ctr[0], 1ull);
+  if (pos >= B.total) return 0;
+  const uint32_t want = (uint32_t)(pos + 1);
+  uint64_t t0 = 0;
+  unsigned ns = 32;
+  for (uint32_t it = 0;; it++) {
+    if (ldcg(B.seq + pos) == want) break;
+    if ((it & 15) == 15) {
+      if (ldcg(B.err) != 0) return -1;
+      const uint64_t now = globaltimer_ns();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > kBatchWaitNs) {
+        atomicOr(B.err, ERR_LOCK);
+        return -1;
+      }
+    }
+    __nanosleep(ns);
+    if (ns < 2048) ns <<= 1;
+  }
+  __threadfence();
+  const uint64_t* src = reinterpret_cast<const uint64_t*>(B.items + pos);
+  uint64_t w0 = ldcg(src), w1 = ldcg(src + 1);
+  out->job = (uint32_t)w0;
+  out->phase = (uint32_t)(w0 >> 32);
+  out->chunk = w1;
+  return 1;
+}
+
+// ---------------------------------------------------------- GEMM chunk
+// One 128 x BNB output tile of C = A Bt^T with the operands staged by the
+// block's threads (plain 16-byte loads into the 128-byte swizzled layout a
+// TMA load would produce), one tcgen05.mma group per 64-wide k-block, the
+// accumulator in TMEM, and a masked epilogue. Any M, N; K % 8 == 0.
+template <uint32_t BNB>
+__device__ bool gemm_chunk(const uint16_t* __restrict__ A, const uint16_t* __restrict__ Bt, float* __restrict__ C,
+                           uint32_t M, uint32_t N, uint32_t K, uint64_t tile, uint32_t sa, uint32_t tmem,
+                           uint32_t mbar, uint32_t& mphase, volatile uint32_t* abort) {
+  const uint32_t nt = (N + BNB - 1) / BNB;
+  const uint32_t m0 = (uint32_t)(tile / nt) * kGemmBM, n0 = (uint32_t)(tile % nt) * BNB;
+  const uint32_t sb = sa + kGemmBM * 128;
+  const uint32_t kbn = (K + 63) / 64;
+  constexpr uint32_t kIdesc = idesc_bf16(kGemmBM, BNB);
+  bool ok = true;
+  for (uint32_t kb = 0; kb < kbn; kb++) {
+    for (uint32_t idx = threadIdx.x; idx < (kGemmBM + BNB) * 8; idx += kChunkThreads) {
+      const bool is_a = idx < kGemmBM * 8;
+      const uint32_t r = (is_a ? idx : idx - kGemmBM * 8) >> 3, c = idx & 7;
+      const uint32_t k = kb * 64 + c * 8;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (is_a) {
+        if (m0 + r < M && k < K) v = *reinterpret_cast<const uint4*>(A + (uint64_t)(m0 + r) * K + k);
+      } else {
+        if (n0 + r < N && k < K) v = *reinterpret_cast<const uint4*>(Bt + (uint64_t)(n0 + r) * K + k);
+      }
+      const uint32_t dst = (is_a ? sa : sb) + r * 128 + ((c ^ (r & 7)) << 4);
+      asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(v.x), "r"(v.y), "r"(v.z),
+                   "r"(v.w)
+                   : "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic stores -> tensor core
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (uint32_t kk = 0; kk < 4; kk++)
+        mma_bf16(tmem, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32), kIdesc, (kb | kk) != 0);
+      mma_commit(mbar);
+    }
+    // every thread waits for the MMAs: the next k-block overwrites the operands
+    const bool done = mbar_wait(mbar, mphase, abort);
+    mphase ^= 1u;
+    tc_fence_after();
+    if (!__syncthreads_and(done)) { ok = false; break; }
+  }
+  if (ok) {
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t q = warp & 3u, half = warp >> 2;
+    const uint32_t row = m0 + q * 32 + lane;
+    for (uint32_t c = half * (BNB / 64); c < (half + 1) * (BNB / 64); c++) {
+      if (n0 + c * 32 >= N) break;
+      uint32_t r[32];
+      tmem_ld_32cols(tmem + ((q * 32u) << 16) + c * 32, r);
+      if (row < M) {
+        float* crow = C + (uint64_t)row * N + n0 + c * 32;
+#pragma unroll
+        for (int v = 0; v < 32; v++)
+          if (n0 + c * 32 + v < N) crow[v] = __uint_as_float(r[v]);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  return ok;
+}
+
+// ---------------------------------------------------------------- kernel
+__global__ void __launch_bounds__(kChunkThreads, 4) k_batch(BatchDev B) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  __shared__ uint64_t T[64];
+  __shared__ uint64_t red[kChunkThreads / 32 + 1];
+  __shared__ uint64_t carry;
+  __shared__ Item cur;
+  __shared__ int action;
+  __shared__ uint32_t s_last;
+  __shared__ uint32_t tmem_base;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ volatile uint32_t s_abort;
+
+  const uint32_t sa = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&mbar), 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(kBatchTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  uint32_t mphase = 0;
+
+  for (;;) {
+    if (threadIdx.x == 0) action = pop(B, &cur);
+    __syncthreads();
+    if (action != 1) break;
+    const Item it = cur;
+    const sg_job& job = B.jobs[it.job];
+    char* base = B.pool + B.offset[it.job];
+    const bool keep = B.keep != nullptr;
+    const uint32_t nph = job_phases(job, keep);
+    const bool digest = keep && it.phase == nph - 1;
+    bool ok = true;
+    if (job.kind == SG_KIND_TRIAD) {
+      const uint64_t n = job.p0;
+      float* a = (float*)base;
+      float* b = a + n;
+      float* c = b + n;
+      const int vec = (n & 3) == 0;            // b and c 16-byte aligned (the grant is)
+      if (digest) digest_chunk((const uint32_t*)a, n, B.keep + it.job, it.chunk);
+      else if (it.phase == 0) gen_triad_chunk(b, c, n, stream_key(job.key, 1), stream_key(job.key, 2), vec, it.chunk);
+      else triad_chunk(a, b, c, 3.0f, n, vec, it.chunk);
+    } else if (job.kind == SG_KIND_GEMM) {
+      const uint32_t m = (uint32_t)job.p0, n = (uint32_t)job.p1, k = job.p2;
+      const GemmLayoutHD L = gemm_layout_hd(m, n, k);
+      uint16_t* A = (uint16_t*)(base + L.A);
+      uint16_t* Bt = (uint16_t*)(base + L.B);
+      float* C = (float*)(base + L.C);
+      if (digest) {
+        digest_chunk((const uint32_t*)C, (uint64_t)m * n, B.keep + it.job, it.chunk);
+      } else if (it.phase == 0) {
+        const uint64_t ca = cdiv((uint64_t)m * k, kBf16Chunk);
+        if (it.chunk < ca) gen_bf16_chunk(A, (uint64_t)m * k, stream_key(job.key, 1), it.chunk);
+        else gen_bf16_chunk(Bt, (uint64_t)n * k, stream_key(job.key, 2), it.chunk - ca);
+      } else if (gemm_bn_small(n) == 128) {
+        ok = gemm_chunk<128>(A, Bt, C, m, n, k, it.chunk, sa, tmem, smem_u32(&mbar), mphase, &s_abort);
+      } else {
+        ok = gemm_chunk<64>(A, Bt, C, m, n, k, it.chunk, sa, tmem, smem_u32(&mbar), mphase, &s_abort);
+      }
+    } else {
+      const uint64_t rows = job.p0, cap = job.p1;
+      const SpmvLayoutHD L = spmv_layout_hd(rows, cap);
+      uint64_t* scan = (uint64_t*)(base + L.scan);
+      const uint64_t lk = stream_key(job.key, 1);
+      if ((it.phase == 0 && it.chunk < L.nchunks) || it.phase == 2) {
+        if (threadIdx.x < 64) T[threadIdx.x] = B.tables[64ull * job.p2 + threadIdx.x];
+        __syncthreads();
+      }
+      if (digest) {
+        digest_chunk((const uint32_t*)(base + L.y), rows, B.keep + it.job, it.chunk);
+      } else if (it.phase == 0) {
+        if (it.chunk < L.nchunks) spmv_chunk_sum(T, lk, rows, scan, it.chunk, red);
+        else spmv_fill_chunk((int32_t*)(base + L.col), (float*)(base + L.val), (float*)(base + L.x), cap, rows,
+                             stream_key(job.key, 2), stream_key(job.key, 3), stream_key(job.key, 4),
+                             it.chunk - L.nchunks);
+      } else if (it.phase == 1) {
+        spmv_scan(scan, L.nchunks, red, &carry);
+      } else if (it.phase == 2) {
+        if (L.ptr64)
+          spmv_row_ptr_chunk<int64_t>(T, lk, rows, scan, L.nchunks, (int64_t*)(base + L.row_ptr), cap, B.err,
+                                      it.chunk, red);
+        else
+          spmv_row_ptr_chunk<int32_t>(T, lk, rows, scan, L.nchunks, (int32_t*)(base + L.row_ptr), cap, B.err,
+                                      it.chunk, red);
+      } else {
+        if (L.ptr64)
+          spmv_chunk<int64_t>((const int64_t*)(base + L.row_ptr), (const int32_t*)(base + L.col),
+                              (const float*)(base + L.val), (const float*)(base + L.x), (float*)(base + L.y), rows,
+                              1, it.chunk);
+        else
+          spmv_chunk<int32_t>((const int32_t*)(base + L.row_ptr), (const int32_t*)(base + L.col),
+                              (const float*)(base + L.val), (const float*)(base + L.x), (float*)(base + L.y), rows,
+                              1, it.chunk);
+      }
+    }
+    if (!ok) {
+      if (threadIdx.x == 0) atomicOr(B.err, 64u);
+      break;
+    }
+    // completion: the block that finishes a phase enqueues the next one; the
+    // one that finishes a job frees its memory for the jobs waiting on it
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      s_last = atomicSub(B.left + it.job, 1u) == 1u;
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      if (it.phase + 1 < nph) {
+        if (threadIdx.x == 0) push_phase(B, it.job, it.phase + 1);
+      } else {
+        for (uint64_t e = B.succ_ptr[it.job] + threadIdx.x; e < B.succ_ptr[it.job + 1]; e += kChunkThreads) {
+          const uint32_t s = B.succ[e];
+          if (atomicSub(B.dep + s, 1u) == 1u) push_phase(B, s, 0);
+        }
+        if (threadIdx.x == 0) atomicAdd(&B.ctr[2], 1ull);
+      }
+    }
+    __syncthreads();
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBatchTmemCols)
+                 : "memory");
+  }
+}
+
+}  // namespace
+}  // namespace sg
+
+using namespace sg;
+
+struct sg_batch {
+  char* dev = nullptr;           // one allocation: every device array below
+  BatchDev d{};
+  uint32_t n = 0, granted = 0;
+  int grid = 0;
+  // launch-time initial state, kept on the device
+  uint32_t* dep0 = nullptr;
+  uint32_t* left0 = nullptr;
+  uint64_t init_items = 0;
+  Item* items0 = nullptr;
+};
+
+extern "C" int sg_batch_build(void* dev_pool, uint64_t pool_bytes, const sg_job* jobs, uint32_t n,
+                              const uint64_t* tables_dev, const sg_record* plan, uint64_t* keep_dev,
+                              sg_batch** out) {
+  if (!out || !dev_pool || (!jobs && n) || (!plan && n)) return SG_ERR_INVALID;
+  *out = nullptr;
+  PlanDeps pd;
+  if (!plan_deps(jobs, n, plan, pool_bytes, &pd)) return SG_ERR_INVALID;
+  const bool keep = keep_dev != nullptr;
+  std::vector<uint8_t> granted(n, 0);
+  uint64_t total = 0;
+  for (uint32_t j : pd.order) {
+    const sg_job& jb = jobs[j];
+    if (jb.kind > SG_KIND_GEMM) return SG_ERR_INVALID;
+    if (jb.kind == SG_KIND_GEMM && (jb.p2 == 0 || jb.p2 % 8 || jb.p0 == 0 || jb.p1 == 0)) return SG_ERR_INVALID;
+    if (jb.kind == SG_KIND_SPMV && (!tables_dev || jb.p0 == 0)) return SG_ERR_INVALID;
+    if (jb.kind == SG_KIND_TRIAD && jb.p0 == 0) return SG_ERR_INVALID;
+    granted[j] = 1;
+    for (uint32_t ph = 0; ph < job_phases(jb, keep); ph++) total += phase_chunks(jb, ph);
+  }
+  // initial state: predecessor counts; phase-0 chunks of jobs with none
+  std::vector<uint32_t> dep0(n, 0), left0(n, 0);
+  std::vector<Item> items0;
+  for (uint32_t j = 0; j < n; j++) dep0[j] = (uint32_t)(pd.pred_ptr[j + 1] - pd.pred_ptr[j]);
+  for (uint32_t j : pd.order) {
+    if (dep0[j] != 0) continue;
+    const uint64_t cnt = phase_chunks(jobs[j], 0);
+    left0[j] = (uint32_t)cnt;
+    for (uint64_t c = 0; c < cnt; c++) items0.push_back(Item{j, 0u, c});
+  }
+  if (total > 0xFFFFFFF0ull) return SG_ERR_CAPACITY;
+  auto a256 = [](uint64_t x) { return (x + 255) / 256 * 256; };
+  const uint64_t nn = n ? n : 1, tt = total ? total : 1;
+  uint64_t o = 0;
+  const uint64_t o_jobs = o; o += a256(sizeof(sg_job) * nn);
+  const uint64_t o_off = o; o += a256(8 * nn);
+  const uint64_t o_sp = o; o += a256(8 * (nn + 1));
+  const uint64_t o_s = o; o += a256(4 * (pd.succ.size() + 1));
+  const uint64_t o_dep = o; o += a256(4 * nn);
+  const uint64_t o_left = o; o += a256(4 * nn);
+  const uint64_t o_dep0 = o; o += a256(4 * nn);
+  const uint64_t o_left0 = o; o += a256(4 * nn);
+  const uint64_t o_items = o; o += a256(sizeof(Item) * tt);
+  const uint64_t o_items0 = o; o += a256(sizeof(Item) * (items0.size() + 1));
+  const uint64_t o_seq = o; o += a256(4 * tt);
+  const uint64_t o_ctr = o; o += 256;
+  const uint64_t o_err = o; o += 256;
+  sg_batch* b = new sg_batch();
+  if (cudaMalloc(&b->dev, o) != cudaSuccess) {
+    delete b;
+    return SG_ERR_CUDA;
+  }
+  char* d = b->dev;
+  std::vector<uint64_t> off(nn, 0);
+  for (uint32_t j = 0; j < n; j++) off[j] = plan[j].offset;
+  bool okc = true;
+  okc &= cudaMemcpy(d + o_jobs, jobs, sizeof(sg_job) * n, cudaMemcpyHostToDevice) == cudaSuccess;
+  okc &= cudaMemcpy(d + o_off, off.data(), 8 * n, cudaMemcpyHostToDevice) == cudaSuccess;
+  okc &= cudaMemcpy(d + o_sp, pd.succ_ptr.data(), 8 * (n + 1), cudaMemcpyHostToDevice) == cudaSuccess;
+  if (!pd.succ.empty())
+    okc &= cudaMemcpy(d + o_s, pd.succ.data(), 4 * pd.succ.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  okc &= cudaMemcpy(d + o_dep0, dep0.data(), 4 * n, cudaMemcpyHostToDevice) == cudaSuccess;
+  okc &= cudaMemcpy(d + o_left0, left0.data(), 4 * n, cudaMemcpyHostToDevice) == cudaSuccess;
+  if (!items0.empty())
+    okc &= cudaMemcpy(d + o_items0, items0.data(), sizeof(Item) * items0.size(), cudaMemcpyHostToDevice) ==
+           cudaSuccess;
+  int per_sm = 0;
+  okc &= cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) == cudaSuccess;
+  okc &= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kChunkThreads, kBatchSmem) == cudaSuccess;
+  if (!okc || per_sm < 1) {
+    cudaFree(b->dev);
+    delete b;
+    return SG_ERR_CUDA;
+  }
+  if (per_sm > 4) per_sm = 4;   // TMEM: 4 x 128 columns per SM
+  b->n = n;
+  b->granted = (uint32_t)pd.order.size();
+  b->grid = per_sm * num_sms();
+  if ((uint64_t)b->grid > total && total > 0) b->grid = (int)total;
+  BatchDev& B = b->d;
+  B.jobs = (const sg_job*)(d + o_jobs);
+  B.offset = (const uint64_t*)(d + o_off);
+  B.pool = (char*)dev_pool;
+  B.tables = tables_dev;
+  B.keep = keep_dev;
+  B.succ_ptr = (const uint64_t*)(d + o_sp);
+  B.succ = (const uint32_t*)(d + o_s);
+  B.dep = (uint32_t*)(d + o_dep);
+  B.left = (uint32_t*)(d + o_left);
+  B.items = (Item*)(d + o_items);
+  B.seq = (uint32_t*)(d + o_seq);
+  B.ctr = (unsigned long long*)(d + o_ctr);
+  B.err = (uint32_t*)(d + o_err);
+  B.total = total;
+  b->dep0 = (uint32_t*)(d + o_dep0);
+  b->left0 = (uint32_t*)(d + o_left0);
+  b->items0 = (Item*)(d + o_items0);
+  b->init_items = items0.size();
+  *out = b;
+  return SG_OK;
+}
+
+__global__ void k_batch_seed(uint32_t* seq, uint64_t init, uint64_t total, unsigned long long* ctr, uint32_t* err) {
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = tid; i < total; i += stride) seq[i] = i < init ? (uint32_t)(i + 1) : 0u;
+  if (tid == 0) {
+    ctr[0] = 0;
+    ctr[1] = init;
+    ctr[2] = 0;
+    *err = 0;
+  }
+}
+
+extern "C" int sg_batch_launch(sg_batch* b, void* stream) {
+  if (!b) return SG_ERR_INVALID;
+  if (b->d.total == 0) return SG_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint32_t n = b->n;
+  if (cudaMemcpyAsync(b->d.dep, b->dep0, 4ull * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(b->d.left, b->left0, 4ull * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return SG_ERR_CUDA;
+  if (b->init_items &&
+      cudaMemcpyAsync(b->d.items, b->items0, sizeof(Item) * b->init_items, cudaMemcpyDeviceToDevice, st) !=
+          cudaSuccess)
+    return SG_ERR_CUDA;
+  if (b->d.keep && cudaMemsetAsync(b->d.keep, 0, 8ull * n, st) != cudaSuccess) return SG_ERR_CUDA;
+  k_batch_seed<<<256, 256, 0, st>>>(b->d.seq, b->init_items, b->d.total, b->d.ctr, b->d.err);
+  if (cudaGetLastError() != cudaSuccess) return SG_ERR_CUDA;
+  void* args[] = {(void*)&b->d};
+  if (cudaLaunchCooperativeKernel((const void*)k_batch, dim3(b->grid), dim3(kChunkThreads), args, kBatchSmem, st) !=
+      cudaSuccess)
+    return SG_ERR_CUDA;
+  return SG_OK;
+}
+
+extern "C" int sg_batch_status(sg_batch* b, uint64_t* jobs_done, uint32_t* err_flags) {
+  if (!b) return SG_ERR_INVALID;
+  unsigned long long c[3] = {0, 0, 0};
+  uint32_t e = 0;
+  if (cudaMemcpy(c, b->d.ctr, sizeof c, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(&e, b->d.err, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return SG_ERR_CUDA;
+  if (jobs_done) *jobs_done = c[2];
+  if (err_flags) *err_flags = e;
+  return (c[2] == b->granted && e == 0) ? SG_OK : SG_ERR_DEVICE;
+}
+
+extern "C" int sg_batch_info(const sg_batch* b, uint64_t* jobs, uint64_t* chunks, uint64_t* blocks) {
+  if (!b) return SG_ERR_INVALID;
+  if (jobs) *jobs = b->granted;
+  if (chunks) *chunks = b->d.total;
+  if (blocks) *blocks = (uint64_t)b->grid;
+  return SG_OK;
+}
+
+extern "C" int sg_batch_destroy(sg_batch* b) {
+  if (!b) return SG_ERR_INVALID;
+  if (b->dev) cudaFree(b->dev);
+  delete b;
+  return SG_OK;
+}

@@ -29,13 +29,15 @@ __device__ __forceinline__ uint64_t round_need(uint64_t need, uint64_t granule) 
 }
 
 __global__ void k_eng_reset(Eng E, uint64_t budget, uint64_t granule, uint32_t policy, uint32_t flags,
-                            uint32_t cap) {
+                            uint32_t cap, uint64_t qt_len) {
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = tid; i < cap; i += stride) {
     E.status[i] = ST_PENDING;
     E.blk_done[i] = 0;
   }
+  for (uint64_t i = tid; i < E.qcap; i += stride) E.qa[i] = kNone;
+  for (uint64_t i = tid; i < qt_len; i += stride) E.qt[i] = kInf;
   if (tid == 0) {
     EngHdr* h = E.hdr;
     h->budget = budget;
@@ -54,6 +56,8 @@ __global__ void k_eng_reset(Eng E, uint64_t budget, uint64_t granule, uint32_t p
     h->q_len = 0;
     h->ring_tail = 0;
     h->n_done = 0;
+    h->q_begin = 0;
+    h->q_end = 0;
     E.ext_off[0] = 0;
     E.ext_len[0] = budget;
   }
@@ -155,12 +159,33 @@ __global__ void k_replay(Eng E, const sg_job* __restrict__ jobs, uint32_t n, uin
 
 // ------------------------------------------------------- device layout
 struct DevLayout {
-  uint64_t hdr, need_g, need_raw, prio, status, blk_done, q, ext_off, ext_len, rec, extra, total;
+  uint64_t hdr, need_g, need_raw, prio, status, blk_done, q, qa, qt, qpos, ext_off, ext_len, rec, extra, total;
+  uint32_t qcap;
+  uint64_t qt_len;
 };
+
+uint32_t queue_positions(uint32_t cap) {
+  uint32_t q = 32;
+  while (q < cap) q <<= 1;
+  return q;
+}
+
+// entries of the 32-ary min-tree over qcap leaves (levels down to <= 32 nodes)
+uint64_t tree_entries(uint32_t qcap) {
+  uint64_t total = 0, size = qcap;
+  for (;;) {
+    total += size;
+    if (size <= 32) break;
+    size >>= 5;
+  }
+  return total;
+}
 
 DevLayout dev_layout(uint32_t cap, bool with_rec, uint64_t extra_bytes) {
   auto a256 = [](uint64_t x) { return (x + 255) / 256 * 256; };
   DevLayout L;
+  L.qcap = queue_positions(cap);
+  L.qt_len = tree_entries(L.qcap);
   uint64_t o = 0;
   L.hdr = o; o += a256(sizeof(EngHdr));
   L.need_g = o; o += a256(8ull * cap);
@@ -169,6 +194,9 @@ DevLayout dev_layout(uint32_t cap, bool with_rec, uint64_t extra_bytes) {
   L.status = o; o += a256(4ull * cap);
   L.blk_done = o; o += a256(4ull * cap);
   L.q = o; o += a256(4ull * (cap + 1));
+  L.qa = o; o += a256(4ull * L.qcap);
+  L.qt = o; o += a256(8ull * L.qt_len);
+  L.qpos = o; o += a256(4ull * cap);
   L.ext_off = o; o += a256(8ull * (cap + 2));
   L.ext_len = o; o += a256(8ull * (cap + 2));
   L.rec = o; if (with_rec) o += a256(sizeof(sg_record) * (uint64_t)cap);
@@ -187,6 +215,10 @@ Eng eng_from(char* base, const DevLayout& L) {
   E.status = (uint32_t*)(base + L.status);
   E.blk_done = (uint32_t*)(base + L.blk_done);
   E.q = (uint32_t*)(base + L.q);
+  E.qa = (uint32_t*)(base + L.qa);
+  E.qt = (uint64_t*)(base + L.qt);
+  E.qpos = (uint32_t*)(base + L.qpos);
+  E.qcap = L.qcap;
   E.ext_off = (uint64_t*)(base + L.ext_off);
   E.ext_len = (uint64_t*)(base + L.ext_len);
   E.rec = (sg_record*)(base + L.rec);
@@ -262,7 +294,8 @@ static void ctx_free(sg_ctx* c) {
 static int ctx_reset_locked(sg_ctx* c) {
   for (auto s : c->slots) CK(cudaStreamSynchronize(s));
   CK(cudaStreamSynchronize(c->ctrl));
-  k_eng_reset<<<64, 256, 0, c->ctrl>>>(c->eng, c->budget, c->granule, c->policy, c->flags, c->cap);
+  k_eng_reset<<<64, 256, 0, c->ctrl>>>(c->eng, c->budget, c->granule, c->policy, c->flags, c->cap,
+                                       c->L.qt_len);
   CK(cudaGetLastError());
   CK(cudaMemsetAsync(c->d_err, 0, 4, c->ctrl));
   CK(cudaStreamSynchronize(c->ctrl));
@@ -654,7 +687,7 @@ extern "C" int sg_replay(const sg_job* jobs_dev, uint32_t n, uint64_t budget, ui
   H.n = 0;
   H.cap = 2 * cap + 1;
   uint64_t b = budget / granule * granule;
-  k_eng_reset<<<8, 256, 0, st>>>(E, b, granule, policy, flags, cap);
+  k_eng_reset<<<8, 256, 0, st>>>(E, b, granule, policy, flags, cap, L.qt_len);
   k_replay<<<1, 32, 0, st>>>(E, jobs_dev, n, exclusive, dur, tmo, H, stats_dev);
   return cudaGetLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
 }
@@ -680,7 +713,7 @@ extern "C" const char* sg_strerror(int code) {
 namespace {
 
 constexpr uint32_t kNoAllocMaxJobs = 16384;
-constexpr uint64_t kNoAllocBytes = 1600ull * 1024;   // >= sg_replay_workspace_bytes(16384)
+constexpr uint64_t kNoAllocBytes = 2048ull * 1024;   // >= sg_replay_workspace_bytes(16384)
 
 // Shared by every call on a device; kept until the process exits.
 static __device__ __align__(256) unsigned char g_replay_scratch[kNoAllocBytes];

@@ -31,7 +31,7 @@ enum : uint32_t { ERR_LOCK = 1u, ERR_STATE = 2u, ERR_ORDER = 4u, ERR_HEAP = 8u, 
 
 struct EngHdr {            // scalar state, device memory
   uint64_t budget, granule, used, seq, peak_used, frag_waits, passes;
-  uint32_t policy, flags, cap, lock, err, n_ext, q_len, ring_tail, n_done, pad;
+  uint32_t policy, flags, cap, lock, err, n_ext, q_len, ring_tail, n_done, q_begin, q_end, pad;
 };
 
 struct Eng {               // array pointers (kernel parameter, by value)
@@ -41,7 +41,11 @@ struct Eng {               // array pointers (kernel parameter, by value)
   int32_t* prio;           // [cap]
   uint32_t* status;        // [cap]
   uint32_t* blk_done;      // [cap] finished blocks of a ticket's final kernel
-  uint32_t* q;             // [cap] waiting tickets in service order
+  uint32_t* q;             // [cap] waiting tickets in service order (priority policies)
+  uint32_t* qa;            // [qcap] FIFO / first fit: ticket at each queue position, or kNone
+  uint64_t* qt;            // 32-ary min-tree over the positions' needs (levels stored back to back)
+  uint32_t* qpos;          // [cap] queue position of a waiting ticket
+  uint32_t qcap;           // positions: a power of two >= max(cap, 32)
   uint64_t* ext_off;       // [cap + 2] free extents, sorted, coalesced
   uint64_t* ext_len;       // [cap + 2]
   sg_record* rec;          // [cap] per-ticket log (device)
@@ -53,8 +57,11 @@ struct Eng {               // array pointers (kernel parameter, by value)
 // Lane-uniform register copy of the scalar state for one locked session.
 struct Sess {
   uint64_t budget, granule, used, seq, peak, frag, passes;
-  uint32_t policy, flags, cap, n_ext, q_len, ring_tail, n_done, err;
+  uint32_t policy, flags, cap, n_ext, q_len, ring_tail, n_done, err, q_begin, q_end;
 };
+
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint64_t kInf = ~0ull;
 
 // Replay only: min-heap of pending completion / timeout events.
 struct EvHeap {
@@ -80,6 +87,8 @@ __device__ __forceinline__ Sess sess_load(const Eng& E) {
   s.q_len = ldcg(&h->q_len);
   s.ring_tail = ldcg(&h->ring_tail);
   s.n_done = ldcg(&h->n_done);
+  s.q_begin = ldcg(&h->q_begin);
+  s.q_end = ldcg(&h->q_end);
   s.err = 0;
   return s;
 }
@@ -97,6 +106,8 @@ __device__ __forceinline__ void sess_store(const Eng& E, const Sess& s) {
     stcg(&h->q_len, s.q_len);
     stcg(&h->ring_tail, s.ring_tail);
     stcg(&h->n_done, s.n_done);
+    stcg(&h->q_begin, s.q_begin);
+    stcg(&h->q_end, s.q_end);
     if (s.err) {
       atomicOr(&h->err, s.err);
       if (E.pub_hdr) atomicOr_system(&E.pub_hdr[1], s.err);
@@ -384,6 +395,8 @@ __device__ __forceinline__ bool try_grant(const Eng& E, Sess& s, uint32_t j, uin
   return true;
 }
 
+// ------------------------------------------------- queue: priority policies
+// The waiting queue in service order as a plain array (sorted insertion).
 __device__ __forceinline__ void q_remove(const Eng& E, Sess& s, uint32_t i) {
   warp_remove_at(E.q, i, s.q_len);
   s.q_len -= 1;
@@ -393,17 +406,95 @@ __device__ __forceinline__ bool is_prio_policy(const Sess& s) {
   return s.policy == SG_POLICY_PRIO_FIFO || s.policy == SG_POLICY_PRIO_FIRST_FIT;
 }
 
+// --------------------------------------------- queue: FIFO and first fit
+// Arrival order never changes under these policies, so every ticket gets the
+// next queue position once and keeps it; a served or withdrawn ticket leaves
+// a hole. A 32-ary tree of minimum needs over the positions answers "first
+// waiter at or after position i whose need is at most F" with one warp-wide
+// load per level, which is exactly the sequential scan of the policy
+// (entries above F fail the count test and are skipped, as in Sec. V).
+__device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    uint64_t w = __shfl_xor_sync(SG_FULL, v, o);
+    v = w < v ? w : v;
+  }
+  return v;
+}
+
+__device__ __forceinline__ void qt_set(const Eng& E, uint64_t pos, uint64_t v) {
+  uint64_t off = 0, size = E.qcap, idx = pos;
+  if (lane_id() == 0) stcg(E.qt + idx, v);
+  __syncwarp();
+  while (size > 32) {
+    const uint64_t block = idx & ~31ull;
+    const uint64_t m = warp_min_u64(ldcg(E.qt + off + block + lane_id()));
+    const uint64_t parent = idx >> 5;
+    off += size;
+    size >>= 5;
+    if (lane_id() == 0) stcg(E.qt + off + parent, m);
+    __syncwarp();
+    idx = parent;
+  }
+}
+
+// first position >= from whose need is <= thr, or -1 (warp-uniform)
+__device__ __forceinline__ int64_t qt_find(const Eng& E, uint64_t from, uint64_t thr) {
+  uint64_t off = 0, size = E.qcap, pos = from;
+  uint32_t level = 0;
+  for (;;) {
+    if (pos >= size) return -1;
+    const uint64_t block = pos & ~31ull, idx = block + lane_id();
+    const bool ok = idx >= pos && idx < size && ldcg(E.qt + off + idx) <= thr;
+    const unsigned m = __ballot_sync(SG_FULL, ok);
+    if (m) { pos = block + (__ffs(m) - 1); break; }
+    if (size <= 32) return -1;
+    pos = (pos >> 5) + 1;
+    off += size;
+    size >>= 5;
+    level++;
+  }
+  while (level > 0) {                     // descend to the first qualifying leaf
+    size <<= 5;
+    off -= size;
+    level--;
+    const uint64_t block = pos << 5, idx = block + lane_id();
+    const bool ok = idx < size && ldcg(E.qt + off + idx) <= thr;
+    const unsigned m = __ballot_sync(SG_FULL, ok);
+    pos = block + (__ffs(m) - 1);         // the parent's minimum guarantees a child
+  }
+  return (int64_t)pos;
+}
+
+__device__ __forceinline__ void qt_remove(const Eng& E, Sess& s, uint32_t pos) {
+  if (lane_id() == 0) stcg(E.qa + pos, kNone);
+  __syncwarp();
+  qt_set(E, pos, kInf);
+  s.q_len -= 1;
+}
+
 __device__ __forceinline__ void q_insert(const Eng& E, Sess& s, uint32_t j) {
-  uint32_t pos = s.q_len;
   if (is_prio_policy(s)) {
     // stable: after every waiter whose priority value is <= j's
     int32_t pj = ldcg(E.prio + j);
     const uint32_t* q = E.q;
     const int32_t* pr = E.prio;
     int64_t p = warp_find_first(0, s.q_len, [&](uint32_t i) { return ldcg(pr + ldcg(q + i)) > pj; });
-    pos = p < 0 ? s.q_len : (uint32_t)p;
+    uint32_t pos = p < 0 ? s.q_len : (uint32_t)p;
+    warp_insert_at(E.q, pos, s.q_len, j);
+  } else {
+    if (s.q_end >= E.qcap) {              // cannot happen: each ticket is queued once
+      s.err |= ERR_CAP;
+      return;
+    }
+    const uint32_t pos = s.q_end++;
+    if (lane_id() == 0) {
+      stcg(E.qa + pos, j);
+      stcg(E.qpos + j, pos);
+    }
+    __syncwarp();
+    qt_set(E, pos, ldcg(E.need_g + j));
   }
-  warp_insert_at(E.q, pos, s.q_len, j);
   s.q_len += 1;
   if (lane_id() == 0) stcg(E.status + j, (uint32_t)ST_QUEUED);
   __syncwarp();
@@ -413,34 +504,37 @@ __device__ __forceinline__ void q_insert(const Eng& E, Sess& s, uint32_t j) {
 __device__ __forceinline__ void policy_pass(const Eng& E, Sess& s, uint64_t t, EvHeap* heap,
                                             const uint64_t* dur) {
   s.passes += 1;
-  const uint32_t* q = E.q;
-  const uint64_t* ng = E.need_g;
-  if (s.policy == SG_POLICY_FIFO || s.policy == SG_POLICY_PRIO_FIFO) {
-    // Policy 1 / 3: serve the head while it fits; stop at the first that does not
+  if (s.policy == SG_POLICY_FIFO) {
+    // Policy 1: serve the head while it fits; stop at the first that does not
+    while (s.q_len > 0) {
+      const int64_t h = qt_find(E, s.q_begin, kInf - 1);
+      if (h < 0) break;
+      s.q_begin = (uint32_t)h;
+      if (!try_grant(E, s, ldcg(E.qa + h), t, heap, dur)) break;
+      qt_remove(E, s, (uint32_t)h);
+    }
+  } else if (s.policy == SG_POLICY_FIRST_FIT) {
+    // Policy 2 (MMU): every waiter that fits, in queue order. Free bytes only
+    // shrink within a pass, so waiters above the free count are skipped.
+    uint64_t i = s.q_begin;
+    while (s.q_len > 0) {
+      const int64_t c = qt_find(E, i, s.budget - s.used);
+      if (c < 0) break;
+      if (try_grant(E, s, ldcg(E.qa + c), t, heap, dur)) qt_remove(E, s, (uint32_t)c);
+      i = (uint64_t)c + 1;
+    }
+  } else if (s.policy == SG_POLICY_PRIO_FIFO) {
+    // Policy 3: FIFO over the queue sorted by (priority, arrival)
+    const uint32_t* q = E.q;
     while (s.q_len > 0) {
       uint32_t h = ldcg(q);
       if (!try_grant(E, s, h, t, heap, dur)) break;
       q_remove(E, s, 0);
     }
-  } else if (s.policy == SG_POLICY_FIRST_FIT) {
-    // Policy 2 (MMU): every waiter that fits, in queue order. Free bytes only
-    // shrink within a pass, so waiters above the free count are skipped.
-    uint32_t i = 0;
-    while (i < s.q_len) {
-      uint64_t freeb = s.budget - s.used;
-      int64_t c = warp_find_first(i, s.q_len, [&](uint32_t k) { return ldcg(ng + ldcg(q + k)) <= freeb; });
-      if (c < 0) break;
-      uint32_t j = ldcg(q + c);
-      if (try_grant(E, s, j, t, heap, dur)) {
-        q_remove(E, s, (uint32_t)c);
-        i = (uint32_t)c;
-      } else {
-        i = (uint32_t)c + 1;
-      }
-    }
   } else {
     // Policy 4: first fit inside the highest-priority class present; the next
     // class is considered only once this one is emptied
+    const uint32_t* q = E.q;
     const int32_t* pr = E.prio;
     while (s.q_len > 0) {
       int32_t p = ldcg(pr + ldcg(q));
@@ -533,9 +627,14 @@ __device__ __forceinline__ uint32_t op_cancel(const Eng& E, Sess& s, uint32_t j,
                                               EvHeap* heap, const uint64_t* dur) {
   uint32_t st = ldcg(E.status + j);
   if (st != ST_QUEUED) return st;
-  const uint32_t* q = E.q;
-  int64_t i = warp_find_first(0, s.q_len, [&](uint32_t k) { return ldcg(q + k) == j; });
-  if (i >= 0) q_remove(E, s, (uint32_t)i);
+  if (is_prio_policy(s)) {
+    const uint32_t* q = E.q;
+    int64_t i = warp_find_first(0, s.q_len, [&](uint32_t k) { return ldcg(q + k) == j; });
+    if (i >= 0) q_remove(E, s, (uint32_t)i);
+  } else {
+    const uint32_t pos = ldcg(E.qpos + j);
+    if (pos < s.q_end && ldcg(E.qa + pos) == j) qt_remove(E, s, pos);
+  }
   sg_record r = rec_load(E, j);
   r.status = ST_TIMEOUT;
   r.done_t = t;

@@ -21,6 +21,7 @@
 
 #include "engine.cuh"
 #include "jobs.h"
+#include "tc.cuh"
 
 namespace sg {
 namespace {
@@ -29,115 +30,10 @@ constexpr int kBM = 128;
 constexpr int kBK = 64;           // 64 bf16 = 128 bytes: one swizzle span
 constexpr int kStages = 4;
 constexpr int kThreadsG = 192;
-constexpr uint64_t kWaitLimitNs = 4000000000ull;
 constexpr int kGroupM = 16;       // tile raster: 16 M-tiles per band
 
 // flags of GEMM kernels that gave up a bounded wait (read by sg_kernel_errors)
 __device__ uint32_t g_tc_err;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t a) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(a), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait; false if it ran out or another role gave up
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile uint32_t* abort) {
-  if (mbar_try(a, parity)) return true;
-  uint64_t t0 = globaltimer_ns();
-  for (uint32_t it = 0;; it++) {
-    if (mbar_try(a, parity)) return true;
-    if ((it & 63) == 63) {
-      if (*abort) return false;
-      if (globaltimer_ns() - t0 > kWaitLimitNs) {
-        *abort = 1;
-        return false;
-      }
-    }
-  }
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y,
-                                            uint32_t mbar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
-      : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// K-major operand in the 128-byte swizzled layout TMA wrote: rows of 128 B,
-// 8-row groups 1024 B apart (stride byte offset), descriptor version 1.
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr >> 4) & 0x3FFFu);         // start address
-  d |= (uint64_t)1 << 16;                         // leading byte offset (unused here)
-  d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset
-  d |= (uint64_t)1 << 46;                         // descriptor version
-  d |= (uint64_t)2 << 61;                         // 128-byte swizzle
-  return d;
-}
-
-// kind::f16 instruction descriptor: BF16 x BF16 -> FP32, both K-major
-__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
-  return (1u << 4)            // D format: F32
-         | (1u << 7)          // A format: BF16
-         | (1u << 10)         // B format: BF16
-         | ((uint32_t)(n >> 3) << 17)
-         | ((uint32_t)(m >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-      ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld_32cols(uint32_t taddr, uint32_t* r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr)
-      : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
 
 __device__ __forceinline__ void tile_coords(uint32_t t, uint32_t mt, uint32_t nt, uint32_t& m, uint32_t& n) {
   uint32_t band = t / (kGroupM * nt);
@@ -335,15 +231,27 @@ bool make_map(CUtensorMap* map, const void* ptr, uint64_t rows, uint64_t K, uint
 }
 
 template <int BN>
-int launch_bn(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, uint32_t N, uint32_t K,
-              const RelHook& h, cudaStream_t st) {
-  constexpr uint32_t smem = kStages * (kBM * kBK * 2 + BN * kBK * 2) + 1024;
+constexpr uint32_t smem_bytes() {
+  return kStages * (kBM * kBK * 2 + BN * kBK * 2) + 1024;
+}
+
+// one-time kernel attribute (outside any stream capture)
+template <int BN>
+int prepare_bn() {
   static std::once_flag once;
   static cudaError_t attr_rc = cudaSuccess;
   std::call_once(once, [] {
-    attr_rc = cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_rc = cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem_bytes<BN>());
   });
-  if (attr_rc != cudaSuccess) return SG_ERR_CUDA;
+  return attr_rc == cudaSuccess ? SG_OK : SG_ERR_CUDA;
+}
+
+template <int BN>
+int launch_bn(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, uint32_t N, uint32_t K,
+              const RelHook& h, cudaStream_t st) {
+  constexpr uint32_t smem = smem_bytes<BN>();
+  if (prepare_bn<BN>() != SG_OK) return SG_ERR_CUDA;
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, M, K, kBM) || !make_map(&mb, Bt, N, K, BN)) return SG_ERR_CUDA;
   uint32_t tiles = ((M + kBM - 1) / kBM) * ((N + BN - 1) / BN);
@@ -367,6 +275,12 @@ int gemm_pick_bn(uint32_t M, uint32_t N) {
     if (waste_ok && mt * nt >= sms) return (int)bn;
   }
   return 64;
+}
+
+int gemm_prepare() {
+  if (!encode_fn()) return SG_ERR_CUDA;
+  if (prepare_bn<64>() != SG_OK || prepare_bn<128>() != SG_OK || prepare_bn<256>() != SG_OK) return SG_ERR_CUDA;
+  return SG_OK;
 }
 
 int launch_gemm_bn(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, uint32_t N, uint32_t K,

@@ -131,3 +131,46 @@ def device_tables(trace: tg.Trace) -> torch.Tensor:
 def records(log: torch.Tensor) -> np.ndarray:
     n = log.numel() // abi.RECORD_DTYPE.itemsize
     return from_device(log, abi.RECORD_DTYPE, n)
+
+
+class Planned:
+    """A batch admitted as a whole by the device engine (a replay plan), run
+    either as one CUDA graph or by the persistent grouped kernel."""
+
+    def __init__(self, pool: torch.Tensor, jobs: np.ndarray, tables: torch.Tensor, policy="first_fit",
+                 keep: bool = False, budget: int | None = None):
+        _require_cuda()
+        self.pool = pool
+        self.jobs = np.ascontiguousarray(jobs, dtype=tg.JOB_DTYPE)
+        self.tables = tables
+        self.budget = budget if budget is not None else pool.numel()
+        self.plan, self.plan_stats = replay(self.jobs, self.budget, policy)
+        self.keep = torch.zeros(len(jobs), dtype=torch.int64, device="cuda") if keep else None
+        kp = self.keep.data_ptr() if keep else 0
+        self.graph = abi.sg_graph_build(pool.data_ptr(), self.budget, self.jobs, tables.data_ptr(), self.plan, kp)
+        self.batch = abi.sg_batch_build(pool.data_ptr(), self.budget, self.jobs, tables.data_ptr(), self.plan, kp)
+
+    def run_graph(self, stream: torch.cuda.Stream | None = None) -> int:
+        if self.keep is not None:
+            self.keep.zero_()
+        return abi.sg_graph_launch(self.graph, stream_handle(stream))
+
+    def run_batch(self, stream: torch.cuda.Stream | None = None) -> int:
+        return abi.sg_batch_launch(self.batch, stream_handle(stream))
+
+    def batch_status(self):
+        return abi.sg_batch_status(self.batch)
+
+    def close(self):
+        if self.graph:
+            abi.sg_graph_destroy(self.graph)
+            self.graph = 0
+        if self.batch:
+            abi.sg_batch_destroy(self.batch)
+            self.batch = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
