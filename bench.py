@@ -281,6 +281,83 @@ def kernel_roofline(torch, abi, peaks):
     return out
 
 
+# ------------------------------------------------------------ batching
+def batching_section(torch, abi, runtime, reps: int = 3) -> dict:
+    """10,000 tiny jobs: one launch per job (online admission) vs one CUDA
+    graph vs the persistent grouped kernel (both on the engine's replay plan)."""
+    tr = tg.trace_c4()
+    n = len(tr)
+    pool = torch.empty(tr.budget, dtype=torch.uint8, device="cuda")
+    tab = runtime.device_tables(tr)
+    out = {"workload": tr.name, "jobs": n}
+    s = runtime.Scheduler(tr.budget, "first_fit", pool=pool)
+    d_jobs = runtime.to_device(tr.jobs)
+    t = []
+    for i in range(reps + 1):
+        rc, _, _, st = s.run_trace(d_jobs, tab, abi.SG_RUN_SATURATED)
+        assert rc == abi.SG_OK
+        if i:
+            t.append(st["elapsed_ns"] * 1e-9)
+    launches = st["launches"]
+    s.shutdown()
+    out["per_job_launch"] = {"jobs_per_s": n / statistics.median(t), "ms": 1e3 * statistics.median(t),
+                             "launches": launches}
+    t0 = time.perf_counter()
+    pl = runtime.Planned(pool, tr.jobs, tab, "first_fit", keep=False, budget=tr.budget)
+    build_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    ms_g = timed(lambda: pl.run_graph())
+    ms_b = timed(lambda: pl.run_batch())
+    rc, done, err = pl.batch_status()
+    assert rc == abi.SG_OK and done == n, (rc, done, err)
+    ginfo = abi.sg_graph_info(pl.graph)
+    binfo = abi.sg_batch_info(pl.batch)
+    out["cuda_graph"] = {"jobs_per_s": n / (ms_g * 1e-3), "ms": ms_g, "kernel_nodes": ginfo["kernels"],
+                         "edges": ginfo["edges"]}
+    out["persistent_kernel"] = {"jobs_per_s": n / (ms_b * 1e-3), "ms": ms_b, "chunks": binfo["chunks"],
+                                "blocks": binfo["blocks"], "launches": 1}
+    out["plan_build_s"] = build_s
+    pl.close()
+    del pool
+    torch.cuda.empty_cache()
+    return out
+
+
+def serving_section(torch, abi, runtime, requests: int, rates=(1000, 2000, 5000, 10000, 20000)) -> dict:
+    """Open-loop serving: Poisson arrivals at each rate, the mixed size mix,
+    64 GiB pool, first fit; requests are declared at their arrival time and
+    admitted as memory frees up while earlier ones run."""
+    out = {"requests_per_rate": requests, "pool_gib": 64, "policy": "first_fit", "rates": {}}
+    s = runtime.Scheduler(64 << 30, "first_fit")
+    for r in rates:
+        tr = tg.trace_c5(n_jobs=requests, rate_per_s=float(r))
+        rc, _, _, st = s.run_trace(runtime.to_device(tr.jobs), runtime.device_tables(tr), abi.SG_RUN_TIMED)
+        assert rc == abi.SG_OK, st
+        out["rates"][str(r)] = {
+            "jobs_per_s": requests / (st["makespan_ns"] * 1e-9),
+            "wait_p50_ms": st["wait_p50_ns"] / 1e6, "wait_p99_ms": st["wait_p99_ns"] / 1e6,
+            "turnaround_p50_ms": st["turnaround_p50_ns"] / 1e6,
+            "turnaround_p99_ms": st["turnaround_p99_ns"] / 1e6,
+            "makespan_ms": st["makespan_ns"] / 1e6, "peak_used_gib": st["peak_used"] / 2 ** 30}
+    s.shutdown()
+    torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
@@ -289,6 +366,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batching and serving sections")
+    ap.add_argument("--serving-requests", type=int, default=4000)
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -380,6 +459,9 @@ def main():
         sched.shutdown()
         del sched
         torch.cuda.empty_cache()
+        if not args.no_extras:
+            extra["batching"] = batching_section(torch, abi, runtime)
+            extra["serving"] = serving_section(torch, abi, runtime, args.serving_requests)
         kr = kernel_roofline(torch, abi, peaks)
         extra["kernels"] = kr
         extra["roofline"] = {k: kr["gemm"][k] for k in ("bound", "achieved", "peak", "unit", "frac",
