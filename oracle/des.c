@@ -48,7 +48,7 @@ typedef struct {
 
 typedef struct {
     uint64_t peak_used;
-    uint64_t frag_waits;     /* count-fit but no extent could hold the request */
+    uint64_t frag_waits;     /* passes that ended blocked by fragmentation (see policy_pass) */
     uint64_t passes;
     uint64_t makespan;       /* last done - first arrival over granted jobs */
 } des_stats;
@@ -145,7 +145,7 @@ static int try_grant(sim_t* s, int j, uint64_t t) {
     uint64_t g = s->need_g[j];
     if (g > s->budget - s->used) return 0;                /* count test */
     uint64_t off;
-    if (!ext_alloc(&s->ext, g, &off)) { s->st->frag_waits++; return 0; }
+    if (!ext_alloc(&s->ext, g, &off)) return 0;       /* fits the count, no extent holds it */
     s->used += g;
     if (s->used > s->st->peak_used) s->st->peak_used = s->used;
     s->out[j].status = ST_RUNNING;
@@ -175,6 +175,22 @@ static void q_insert(sim_t* s, int j) {
     s->out[j].status = ST_QUEUED;
 }
 
+static int count_fits(const sim_t* s, int j) { return s->need_g[j] <= s->budget - s->used; }
+
+/* A pass ends blocked by fragmentation when a waiter the policy would serve
+ * next fits the free byte count but no free extent can hold it: the head
+ * under FIFO and Priority FIFO, any waiter under first fit, any waiter of
+ * the top class under Priority MMU. */
+static int blocked_by_fragmentation(const sim_t* s) {
+    if (s->qn == 0) return 0;
+    if (s->policy == POL_FIFO || s->policy == POL_PRIO_FIFO) return count_fits(s, s->q[0]);
+    for (int i = 0; i < s->qn; i++) {
+        if (s->policy == POL_PRIO_FIRST_FIT && s->prio[s->q[i]] != s->prio[s->q[0]]) break;
+        if (count_fits(s, s->q[i])) return 1;
+    }
+    return 0;
+}
+
 /* One notification pass over the waiting queue at time t. */
 static void policy_pass(sim_t* s, uint64_t t) {
     s->st->passes++;
@@ -201,6 +217,7 @@ static void policy_pass(sim_t* s, uint64_t t) {
             if (s->qn > 0 && s->prio[s->q[0]] == p) break;   /* class not emptied */
         }
     }
+    if (blocked_by_fragmentation(s)) s->st->frag_waits++;
 }
 
 int des_run(int n, const uint64_t* arrival, const uint64_t* need, const uint64_t* duration,

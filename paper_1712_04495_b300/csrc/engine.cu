@@ -60,6 +60,7 @@ __global__ void k_eng_reset(Eng E, uint64_t budget, uint64_t granule, uint32_t p
     h->q_end = 0;
     E.ext_off[0] = 0;
     E.ext_len[0] = budget;
+    h->max_ext = budget;
   }
 }
 

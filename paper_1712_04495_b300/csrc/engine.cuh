@@ -32,6 +32,7 @@ enum : uint32_t { ERR_LOCK = 1u, ERR_STATE = 2u, ERR_ORDER = 4u, ERR_HEAP = 8u, 
 struct EngHdr {            // scalar state, device memory
   uint64_t budget, granule, used, seq, peak_used, frag_waits, passes;
   uint32_t policy, flags, cap, lock, err, n_ext, q_len, ring_tail, n_done, q_begin, q_end, pad;
+  uint64_t max_ext;        // length of the largest free extent
 };
 
 struct Eng {               // array pointers (kernel parameter, by value)
@@ -56,7 +57,7 @@ struct Eng {               // array pointers (kernel parameter, by value)
 
 // Lane-uniform register copy of the scalar state for one locked session.
 struct Sess {
-  uint64_t budget, granule, used, seq, peak, frag, passes;
+  uint64_t budget, granule, used, seq, peak, frag, passes, max_ext;
   uint32_t policy, flags, cap, n_ext, q_len, ring_tail, n_done, err, q_begin, q_end;
 };
 
@@ -89,6 +90,7 @@ __device__ __forceinline__ Sess sess_load(const Eng& E) {
   s.n_done = ldcg(&h->n_done);
   s.q_begin = ldcg(&h->q_begin);
   s.q_end = ldcg(&h->q_end);
+  s.max_ext = ldcg(&h->max_ext);
   s.err = 0;
   return s;
 }
@@ -108,6 +110,7 @@ __device__ __forceinline__ void sess_store(const Eng& E, const Sess& s) {
     stcg(&h->n_done, s.n_done);
     stcg(&h->q_begin, s.q_begin);
     stcg(&h->q_end, s.q_end);
+    stcg(&h->max_ext, s.max_ext);
     if (s.err) {
       atomicOr(&h->err, s.err);
       if (E.pub_hdr) atomicOr_system(&E.pub_hdr[1], s.err);
@@ -199,6 +202,22 @@ __device__ __forceinline__ int64_t ext_find(const Eng& E, const Sess& s, uint64_
   return warp_find_first(0, s.n_ext, [&](uint32_t i) { return ldcg(len + i) >= g; });
 }
 
+// largest free extent (warp-wide maximum over the list)
+__device__ __forceinline__ uint64_t ext_max(const Eng& E, const Sess& s) {
+  uint64_t m = 0;
+  for (uint32_t base = 0; base < s.n_ext; base += 32) {
+    const uint32_t i = base + lane_id();
+    const uint64_t v = i < s.n_ext ? ldcg(E.ext_len + i) : 0;
+    m = v > m ? v : m;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const uint64_t w = __shfl_xor_sync(SG_FULL, m, o);
+    m = w > m ? w : m;
+  }
+  return m;
+}
+
 // take g bytes from the front of extent e
 __device__ __forceinline__ uint64_t ext_take(const Eng& E, Sess& s, uint32_t e, uint64_t g) {
   uint64_t off = ldcg(E.ext_off + e);
@@ -215,6 +234,7 @@ __device__ __forceinline__ uint64_t ext_take(const Eng& E, Sess& s, uint32_t e, 
     }
     __syncwarp();
   }
+  if (len == s.max_ext) s.max_ext = ext_max(E, s);   // the largest one shrank
   return off;
 }
 
@@ -236,23 +256,28 @@ __device__ __forceinline__ void ext_give(const Eng& E, Sess& s, uint64_t off, ui
     right = off + g == ro;
   }
   __syncwarp();
+  uint64_t merged = g;
   if (left && right) {
-    if (lane_id() == 0) stcg(E.ext_len + ip - 1, ll + g + rl);
+    merged = ll + g + rl;
+    if (lane_id() == 0) stcg(E.ext_len + ip - 1, merged);
     __syncwarp();
     warp_remove_at(E.ext_off, ip, s.n_ext);
     warp_remove_at(E.ext_len, ip, s.n_ext);
     s.n_ext -= 1;
   } else if (left) {
-    if (lane_id() == 0) stcg(E.ext_len + ip - 1, ll + g);
+    merged = ll + g;
+    if (lane_id() == 0) stcg(E.ext_len + ip - 1, merged);
     __syncwarp();
   } else if (right) {
-    if (lane_id() == 0) { stcg(E.ext_off + ip, off); stcg(E.ext_len + ip, rl + g); }
+    merged = rl + g;
+    if (lane_id() == 0) { stcg(E.ext_off + ip, off); stcg(E.ext_len + ip, merged); }
     __syncwarp();
   } else {
     warp_insert_at(E.ext_off, ip, s.n_ext, off);
     warp_insert_at(E.ext_len, ip, s.n_ext, g);
     s.n_ext += 1;
   }
+  if (merged > s.max_ext) s.max_ext = merged;
 }
 
 // ----------------------------------------------------------- publication
@@ -374,8 +399,9 @@ __device__ __forceinline__ bool try_grant(const Eng& E, Sess& s, uint32_t j, uin
                                           EvHeap* heap, const uint64_t* dur) {
   uint64_t g = ldcg(E.need_g + j);
   if (g > s.budget - s.used) return false;              // count test (Sec. III-B)
+  if (g > s.max_ext) return false;                      // fits the count, no extent holds it
   int64_t e = ext_find(E, s, g);
-  if (e < 0) { s.frag += 1; return false; }              // count-fits, cannot be placed
+  if (e < 0) { s.err |= ERR_STATE; return false; }      // the largest extent would hold it
   uint64_t off = ext_take(E, s, (uint32_t)e, g);
   s.used += g;
   if (s.used > s.peak) s.peak = s.used;
@@ -516,9 +542,12 @@ __device__ __forceinline__ void policy_pass(const Eng& E, Sess& s, uint64_t t, E
   } else if (s.policy == SG_POLICY_FIRST_FIT) {
     // Policy 2 (MMU): every waiter that fits, in queue order. Free bytes only
     // shrink within a pass, so waiters above the free count are skipped.
+    // Waiters above the largest free extent cannot be placed either, so the
+    // search skips them too and every waiter it finds is served.
     uint64_t i = s.q_begin;
     while (s.q_len > 0) {
-      const int64_t c = qt_find(E, i, s.budget - s.used);
+      const uint64_t freeb = s.budget - s.used;
+      const int64_t c = qt_find(E, i, freeb < s.max_ext ? freeb : s.max_ext);
       if (c < 0) break;
       if (try_grant(E, s, ldcg(E.qa + c), t, heap, dur)) qt_remove(E, s, (uint32_t)c);
       i = (uint64_t)c + 1;
@@ -547,6 +576,32 @@ __device__ __forceinline__ void policy_pass(const Eng& E, Sess& s, uint64_t t, E
       }
       if (s.q_len > 0 && ldcg(pr + ldcg(q)) == p) break;
     }
+  }
+  // A pass ends blocked by fragmentation when a waiter the policy would serve
+  // next fits the free byte count but no free extent holds it: the head under
+  // FIFO and Priority FIFO, any waiter under first fit, any waiter of the top
+  // class under Priority MMU.
+  if (s.q_len > 0) {
+    const uint64_t freeb = s.budget - s.used;
+    const uint64_t* ng = E.need_g;
+    bool blocked = false;
+    if (s.policy == SG_POLICY_FIFO) {
+      const int64_t h = qt_find(E, s.q_begin, kInf - 1);
+      blocked = h >= 0 && ldcg(E.need_g + ldcg(E.qa + h)) <= freeb;
+    } else if (s.policy == SG_POLICY_FIRST_FIT) {
+      blocked = qt_find(E, s.q_begin, freeb) >= 0;
+    } else if (s.policy == SG_POLICY_PRIO_FIFO) {
+      blocked = ldcg(ng + ldcg(E.q)) <= freeb;
+    } else {
+      const uint32_t* q = E.q;
+      const int32_t* pr = E.prio;
+      const int32_t p = ldcg(pr + ldcg(q));
+      blocked = warp_find_first(0, s.q_len, [&](uint32_t k) {
+                  const uint32_t j = ldcg(q + k);
+                  return ldcg(pr + j) == p && ldcg(ng + j) <= freeb;
+                }) >= 0;
+    }
+    if (blocked) s.frag += 1;
   }
 }
 
