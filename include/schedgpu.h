@@ -310,9 +310,22 @@ int sg_gemm_bf16(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, ui
  * columns per 128-row tile (0 = the built-in choice, sg_gemm_tile_n). */
 int sg_gemm_bf16_tiled(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, uint32_t N,
                        uint32_t K, uint32_t tile_n, void* stream);
-/* The tile width sg_gemm_bf16 picks for an M x N output: the widest that
- * still gives every SM a tile with at most 1/8 of it wasted. Host only. */
+/* The tile width sg_gemm_bf16 uses for an M x N output: the autotuner's
+ * choice if it has tuned that shape, else the widest that still gives
+ * every SM a tile with at most 1/8 of it wasted. Host only. */
 uint32_t sg_gemm_tile_n(uint32_t M, uint32_t N);
+
+/* Autotuner for the GEMM tile width. shapes: n_shapes (M, N, K) triples
+ * (host). For each shape, generates inputs in `scratch` (device, needs
+ * 2MK + 2NK + 4MN bytes rounded to 256 B per array; shapes that do not fit
+ * are skipped with chosen = 0), times every width (one warm-up, median of
+ * three CUDA-event timings on `stream`) and records the fastest for (M, N)
+ * in a process-wide table used by every later GEMM launch. chosen / best_ms
+ * (host, n_shapes each) may be NULL. Synchronous. */
+int sg_autotune_gemm(const uint32_t* shapes, uint32_t n_shapes, void* scratch, uint64_t scratch_bytes,
+                     uint32_t* chosen, float* best_ms, void* stream);
+/* Forget every tuned shape. */
+int sg_autotune_clear(void);
 
 /* GEMM inputs: A[i,k] = bf16(U(stream 1, i*K+k)), Bt[j,k] = bf16(U(stream 2, j*K+k)). */
 int sg_gen_gemm(uint16_t* A, uint16_t* Bt, uint32_t M, uint32_t N, uint32_t K, uint64_t key,

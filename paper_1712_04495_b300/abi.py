@@ -97,6 +97,8 @@ _SIGS = {
     "sg_gemm_bf16": ([_P, _P, _P, _U32, _U32, _U32, _P], ctypes.c_int),
     "sg_gemm_bf16_tiled": ([_P, _P, _P, _U32, _U32, _U32, _U32, _P], ctypes.c_int),
     "sg_gemm_tile_n": ([_U32, _U32], _U32),
+    "sg_autotune_gemm": ([_P, _U32, _P, _U64, _P, _P, _P], ctypes.c_int),
+    "sg_autotune_clear": ([], ctypes.c_int),
     "sg_gen_gemm": ([_P, _P, _U32, _U32, _U32, _U64, _P], ctypes.c_int),
     "sg_digest": ([_P, _U64, _P, _P], ctypes.c_int),
 }
@@ -300,6 +302,21 @@ def sg_gemm_bf16_tiled(A, Bt, C, M: int, N: int, K: int, tile_n: int, stream: in
 
 def sg_gemm_tile_n(M: int, N: int) -> int:
     return lib().sg_gemm_tile_n(M, N)
+
+
+def sg_autotune_gemm(shapes, scratch_ptr: int, scratch_bytes: int, stream: int = 0):
+    """Tune the tile width of each (M, N, K); returns [(shape, width, ms)]."""
+    arr = np.ascontiguousarray(np.asarray(shapes, dtype=np.uint32).reshape(-1, 3))
+    n = len(arr)
+    chosen = np.zeros(n, dtype=np.uint32)
+    best = np.zeros(n, dtype=np.float32)
+    _check(lib().sg_autotune_gemm(arr.ctypes.data, n, scratch_ptr, scratch_bytes, chosen.ctypes.data,
+                                  best.ctypes.data, stream), "sg_autotune_gemm")
+    return [(tuple(int(x) for x in arr[i]), int(chosen[i]), float(best[i])) for i in range(n)]
+
+
+def sg_autotune_clear():
+    _check(lib().sg_autotune_clear(), "sg_autotune_clear")
 
 
 def sg_gen_gemm(A, Bt, M: int, N: int, K: int, key: int, stream: int = 0) -> int:

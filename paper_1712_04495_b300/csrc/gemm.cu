@@ -289,6 +289,7 @@ int launch_gemm_bn(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, 
   if (K == 0 || K % 8) return SG_ERR_INVALID;       // TMA row stride: a multiple of 16 bytes
   if (((uintptr_t)A & 15) || ((uintptr_t)Bt & 15) || ((uintptr_t)C & 15)) return SG_ERR_INVALID;
   if (!encode_fn()) return SG_ERR_CUDA;
+  if (bn <= 0) bn = tuned_tile_n(M, N);
   if (bn <= 0) bn = gemm_pick_bn(M, N);
   if (bn == 256) return launch_bn<256>(A, Bt, C, M, N, K, h, st);
   if (bn == 128) return launch_bn<128>(A, Bt, C, M, N, K, h, st);
@@ -320,7 +321,10 @@ extern "C" int sg_gemm_bf16_tiled(const uint16_t* A, const uint16_t* Bt, float* 
   return sg::launch_gemm_bn(A, Bt, C, M, N, K, (int)tile_n, h, (cudaStream_t)stream);
 }
 
-extern "C" uint32_t sg_gemm_tile_n(uint32_t M, uint32_t N) { return (uint32_t)sg::gemm_pick_bn(M, N); }
+extern "C" uint32_t sg_gemm_tile_n(uint32_t M, uint32_t N) {
+  const int t = sg::tuned_tile_n(M, N);
+  return (uint32_t)(t > 0 ? t : sg::gemm_pick_bn(M, N));
+}
 
 extern "C" int sg_kernel_errors(uint32_t* flags_out) {
   if (!flags_out) return SG_ERR_INVALID;

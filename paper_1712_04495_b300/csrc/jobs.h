@@ -35,6 +35,8 @@ int launch_gemm(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, uin
 int launch_gemm_bn(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, uint32_t N, uint32_t K,
                    int bn, const RelHook& h, cudaStream_t st);
 int gemm_pick_bn(uint32_t M, uint32_t N);
+// width the autotuner recorded for an M x N output, or 0 (autotune.cu)
+int tuned_tile_n(uint32_t M, uint32_t N);
 // driver entry point and kernel attributes, once (call before stream capture)
 int gemm_prepare();
 

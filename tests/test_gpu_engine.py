@@ -160,3 +160,40 @@ def test_timed_arrivals():
     span = int(tr.jobs["arrival_ns"][-1])
     assert st["makespan_ns"] >= span * 0.9
     s.shutdown()
+
+
+def test_priority_fifo_serves_higher_priority_first():
+    abi, rt = _rt()
+    s = rt.Scheduler(MIB, "prio_fifo")
+    t1 = s.declare(900 * 1024)
+    assert s.wait(t1, 10 ** 9)[0] == abi.SG_OK
+    t2 = s.declare(600 * 1024, priority=1)
+    t3 = s.declare(600 * 1024, priority=0)      # smaller value = higher priority
+    torch.cuda.synchronize()
+    assert s.try_grant(t2)[0] == abi.SG_NOT_READY and s.try_grant(t3)[0] == abi.SG_NOT_READY
+    s.release(t1)
+    rc, g3 = s.wait(t3, 10 ** 9)
+    assert rc == abi.SG_OK and g3.offset == 0
+    assert s.try_grant(t2)[0] == abi.SG_NOT_READY
+    s.release(t3)
+    assert s.wait(t2, 10 ** 9)[0] == abi.SG_OK
+    s.shutdown()
+
+
+def test_serving_results_equal_alone_and_in_the_mix():
+    # open-loop arrivals admitted while earlier requests run; every request's
+    # output equals its output when it runs alone on the GPU
+    abi, rt = _rt()
+    budget = 48 * MIB
+    tr = tg.trace_mixed(21, 60, 3000.0, budget, "serve_small", triad_rng=(1 << 16, 1 << 20),
+                        spmv_rng=(2e3, 4e4), gemm_set=(128, 256, 512))
+    s = rt.Scheduler(budget, "first_fit")
+    d_jobs, d_tab = rt.to_device(tr.jobs), rt.device_tables(tr)
+    rc, log, keep_mix, st = s.run_trace(d_jobs, d_tab, abi.SG_RUN_TIMED, keep=True)
+    assert rc == abi.SG_OK
+    rec = rt.records(log)
+    _check_real_log(tr.jobs, rec, budget, "first_fit")
+    rc, _, keep_alone, _ = s.run_trace(d_jobs, d_tab, abi.SG_RUN_SATURATED | abi.SG_RUN_EXCLUSIVE, keep=True)
+    assert rc == abi.SG_OK
+    assert torch.equal(keep_mix, keep_alone)
+    s.shutdown()

@@ -188,3 +188,22 @@ def test_digest_is_order_free_sum():
     with np.errstate(over="ignore"):
         ref = np.sum(tg.mix64((np.arange(n, dtype=np.uint64) << np.uint64(32)) | w), dtype=np.uint64)
     assert int(out.item()) & ((1 << 64) - 1) == int(ref)
+
+
+def test_autotuner_picks_a_width_and_gemm_stays_exact():
+    abi = _abi()
+    scratch = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")
+    try:
+        res = abi.sg_autotune_gemm([(256, 256, 256), (512, 384, 64), (8192, 8192, 8192)], scratch.data_ptr(),
+                                   scratch.numel())
+        assert res[0][1] in (64, 128, 256) and res[0][2] > 0
+        assert res[1][1] in (64, 128, 256)
+        assert res[2][1] == 0                      # does not fit the scratch: skipped
+        assert abi.sg_gemm_tile_n(256, 256) == res[0][1]
+        key = 5
+        A, Bt, C = _gemm(512, 384, 64, key)       # uses the tuned width
+        ref = K.gemm(key, 512, 384, 64)
+        assert np.linalg.norm(C.cpu().numpy() - ref) / np.linalg.norm(ref) <= 1e-5
+    finally:
+        abi.sg_autotune_clear()
+    assert abi.sg_gemm_tile_n(256, 256) == 64
