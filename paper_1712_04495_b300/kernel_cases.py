@@ -4,6 +4,10 @@
     python -m paper_1712_04495_b300.kernel_cases spmv  [rows, default 1e7]   [launches]
     python -m paper_1712_04495_b300.kernel_cases triad [n, default 64M]      [launches]
     python -m paper_1712_04495_b300.kernel_cases fill  [rows, default 1e7]   [launches]
+    python -m paper_1712_04495_b300.kernel_cases batch [jobs, default 10000] [launches]
+
+`batch` runs the tiny-job trace (10,000 jobs, 2 GiB pool) through the
+persistent grouped kernel on the device engine's replay plan.
 
 The inputs are built by the library's own generators first (one launch per
 generator kernel), then the kernel runs `launches` times (default 3) on the
@@ -71,6 +75,16 @@ def run(kind: str, size: int | None = None, launches: int = 3) -> dict:
         assert abi.sg_gen_triad(b.data_ptr(), c.data_ptr(), n, 7, st) == 0
         ms = _time(lambda: abi.sg_triad(a.data_ptr(), b.data_ptr(), c.data_ptr(), 3.0, n, st), launches)
         return {"kernel": "triad", "n": n, "ms": ms, "gbs": 12.0 * n / (ms * 1e-3) / 1e9}
+    if kind == "batch":
+        from . import runtime
+        tr = tg.trace_c4(n_jobs=size or 10_000)
+        pool = torch.empty(tr.budget, dtype=torch.uint8, device="cuda")
+        pl = runtime.Planned(pool, tr.jobs, runtime.device_tables(tr), "first_fit", budget=tr.budget)
+        ms = _time(lambda: pl.run_batch(), launches)
+        rc, done, err = pl.batch_status()
+        info = abi.sg_batch_info(pl.batch)
+        pl.close()
+        return {"kernel": "batch", "jobs": len(tr), "ms": ms, "done": done, "err": err, **info}
     raise ValueError(kind)
 
 
