@@ -433,6 +433,9 @@ extern "C" int sg_batch_build(void* dev_pool, uint64_t pool_bytes, const sg_job*
            cudaSuccess;
   int per_sm = 0;
   okc &= cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) == cudaSuccess;
+  // the largest shared-memory split, so four blocks (and their TMEM) fit an SM
+  okc &= cudaFuncSetAttribute(k_batch, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess;
   okc &= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kChunkThreads, kBatchSmem) == cudaSuccess;
   if (!okc || per_sm < 1) {
     cudaFree(b->dev);
