@@ -437,12 +437,15 @@ extern "C" int sg_batch_build(void* dev_pool, uint64_t pool_bytes, const sg_job*
   okc &= cudaFuncSetAttribute(k_batch, cudaFuncAttributePreferredSharedMemoryCarveout,
                               (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess;
   okc &= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kChunkThreads, kBatchSmem) == cudaSuccess;
-  if (!okc || per_sm < 1) {
+  if (!okc) {
     cudaFree(b->dev);
     delete b;
     return SG_ERR_CUDA;
   }
-  if (per_sm > 4) per_sm = 4;   // TMEM: 4 x 128 columns per SM
+  // The kernel's registers and shared memory admit at most 4 blocks per SM,
+  // exactly what TMEM allows (4 x 128 columns); the launch steps down if the
+  // cooperative launch reports that the grid does not fit.
+  per_sm = 4;
   b->n = n;
   b->granted = (uint32_t)pd.order.size();
   b->grid = per_sm * num_sms();
@@ -498,10 +501,14 @@ extern "C" int sg_batch_launch(sg_batch* b, void* stream) {
   k_batch_seed<<<256, 256, 0, st>>>(b->d.seq, b->init_items, b->d.total, b->d.ctr, b->d.err);
   if (cudaGetLastError() != cudaSuccess) return SG_ERR_CUDA;
   void* args[] = {(void*)&b->d};
-  if (cudaLaunchCooperativeKernel((const void*)k_batch, dim3(b->grid), dim3(kChunkThreads), args, kBatchSmem, st) !=
-      cudaSuccess)
-    return SG_ERR_CUDA;
-  return SG_OK;
+  for (;;) {
+    const cudaError_t e =
+        cudaLaunchCooperativeKernel((const void*)k_batch, dim3(b->grid), dim3(kChunkThreads), args, kBatchSmem, st);
+    if (e == cudaSuccess) return SG_OK;
+    if (e != cudaErrorCooperativeLaunchTooLarge || b->grid <= num_sms()) return SG_ERR_CUDA;
+    cudaGetLastError();
+    b->grid -= num_sms();                     // one block fewer per SM
+  }
 }
 
 extern "C" int sg_batch_status(sg_batch* b, uint64_t* jobs_done, uint32_t* err_flags) {
