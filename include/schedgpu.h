@@ -263,7 +263,8 @@ int sg_batch_build(void* dev_pool, uint64_t pool_bytes, const sg_job* jobs, uint
                    sg_batch** out);
 int sg_batch_launch(sg_batch* b, void* stream);
 int sg_batch_status(sg_batch* b, uint64_t* jobs_done, uint32_t* err_flags);
-int sg_batch_info(const sg_batch* b, uint64_t* jobs, uint64_t* chunks, uint64_t* blocks);
+/* jobs planned, chunks in the batch, workers (four per SM) of the launch */
+int sg_batch_info(const sg_batch* b, uint64_t* jobs, uint64_t* chunks, uint64_t* workers);
 int sg_batch_destroy(sg_batch* b);
 
 /* Engine error flags of the context (0 = none). */

@@ -33,8 +33,14 @@ namespace sg {
 namespace {
 
 constexpr uint64_t kBatchWaitNs = 20000000000ull;  // 20 s for one queue slot
-constexpr uint32_t kBatchSmem = 50 * 1024;          // also caps residency at 4 blocks / SM
-constexpr uint32_t kBatchTmemCols = 128;            // 4 blocks x 128 = the SM's 512 columns
+// A kernel that allocates TMEM gets one block per SM, so each block holds
+// four independent workers of kChunkThreads threads (named barriers 1..4),
+// each with its own GEMM staging buffers and 128 of the SM's 512 TMEM columns.
+constexpr uint32_t kGroups = 4;
+constexpr uint32_t kBatchThreads = kGroups * kChunkThreads;
+constexpr uint32_t kGemmSmem = 32 * 1024;           // per worker: A 16 KiB + B (<= 128 rows) 16 KiB
+constexpr uint32_t kBatchSmem = kGroups * kGemmSmem + 1024;
+constexpr uint32_t kBatchTmemCols = 512;
 constexpr uint32_t kGemmBM = 128;
 
 struct Item {
@@ -145,13 +151,14 @@ __device__ int pop(const BatchDev& B, Item* out) {
 
 // ---------------------------------------------------------- GEMM chunk
 // One 128 x BNB output tile of C = A Bt^T with the operands staged by the
-// block's threads (plain 16-byte loads into the 128-byte swizzled layout a
+// worker's threads (plain 16-byte loads into the 128-byte swizzled layout a
 // TMA load would produce), one tcgen05.mma group per 64-wide k-block, the
-// accumulator in TMEM, and a masked epilogue. Any M, N; K % 8 == 0.
-template <uint32_t BNB>
-__device__ bool gemm_chunk(const uint16_t* __restrict__ A, const uint16_t* __restrict__ Bt, float* __restrict__ C,
-                           uint32_t M, uint32_t N, uint32_t K, uint64_t tile, uint32_t sa, uint32_t tmem,
-                           uint32_t mbar, uint32_t& mphase, volatile uint32_t* abort) {
+// accumulator in the worker's TMEM columns, and a masked epilogue. Any M, N;
+// K % 8 == 0.
+template <uint32_t BNB, class G>
+__device__ bool gemm_chunk(const G& g, const uint16_t* __restrict__ A, const uint16_t* __restrict__ Bt,
+                           float* __restrict__ C, uint32_t M, uint32_t N, uint32_t K, uint64_t tile, uint32_t sa,
+                           uint32_t tmem, uint32_t mbar, uint32_t& mphase, volatile uint32_t* abort, int* vote) {
   const uint32_t nt = (N + BNB - 1) / BNB;
   const uint32_t m0 = (uint32_t)(tile / nt) * kGemmBM, n0 = (uint32_t)(tile % nt) * BNB;
   const uint32_t sb = sa + kGemmBM * 128;
@@ -159,7 +166,7 @@ __device__ bool gemm_chunk(const uint16_t* __restrict__ A, const uint16_t* __res
   constexpr uint32_t kIdesc = idesc_bf16(kGemmBM, BNB);
   bool ok = true;
   for (uint32_t kb = 0; kb < kbn; kb++) {
-    for (uint32_t idx = threadIdx.x; idx < (kGemmBM + BNB) * 8; idx += kChunkThreads) {
+    for (uint32_t idx = g.t(); idx < (kGemmBM + BNB) * 8; idx += kChunkThreads) {
       const bool is_a = idx < kGemmBM * 8;
       const uint32_t r = (is_a ? idx : idx - kGemmBM * 8) >> 3, c = idx & 7;
       const uint32_t k = kb * 64 + c * 8;
@@ -175,8 +182,8 @@ __device__ bool gemm_chunk(const uint16_t* __restrict__ A, const uint16_t* __res
                    : "memory");
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic stores -> tensor core
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    g.sync();
+    if (g.t() == 0) {
       tc_fence_after();
 #pragma unroll
       for (uint32_t kk = 0; kk < 4; kk++)
@@ -187,11 +194,17 @@ __device__ bool gemm_chunk(const uint16_t* __restrict__ A, const uint16_t* __res
     const bool done = mbar_wait(mbar, mphase, abort);
     mphase ^= 1u;
     tc_fence_after();
-    if (!__syncthreads_and(done)) { ok = false; break; }
+    if (g.t() == 0) *vote = 1;
+    g.sync();
+    if (!done) *vote = 0;
+    g.sync();
+    const bool all = *vote != 0;
+    g.sync();
+    if (!all) { ok = false; break; }
   }
   if (ok) {
-    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t q = warp & 3u, half = warp >> 2;
+    const uint32_t warp = g.t() >> 5, lane = g.t() & 31;
+    const uint32_t q = warp & 3u, half = warp >> 2;   // the group's warps start at a multiple of 4
     const uint32_t row = m0 + q * 32 + lane;
     for (uint32_t c = half * (BNB / 64); c < (half + 1) * (BNB / 64); c++) {
       if (n0 + c * 32 >= N) break;
@@ -206,26 +219,29 @@ __device__ bool gemm_chunk(const uint16_t* __restrict__ A, const uint16_t* __res
     }
   }
   tc_fence_before();
-  __syncthreads();
+  g.sync();
   return ok;
 }
 
 // ---------------------------------------------------------------- kernel
-__global__ void __launch_bounds__(kChunkThreads, 4) k_batch(BatchDev B) {
+__global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchDev B) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  __shared__ uint64_t T[64];
-  __shared__ uint64_t red[kChunkThreads / 32 + 1];
-  __shared__ uint64_t carry;
-  __shared__ Item cur;
-  __shared__ int action;
-  __shared__ uint32_t s_last;
+  __shared__ uint64_t T[kGroups][64];
+  __shared__ uint64_t red[kGroups][kChunkThreads / 32 + 1];
+  __shared__ uint64_t carry[kGroups];
+  __shared__ Item cur[kGroups];
+  __shared__ int action[kGroups];
+  __shared__ uint32_t s_last[kGroups];
+  __shared__ int vote[kGroups];
   __shared__ uint32_t tmem_base;
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar[kGroups];
   __shared__ volatile uint32_t s_abort;
 
-  const uint32_t sa = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const uint32_t gi = threadIdx.x / kChunkThreads;
+  const SubGroup g{gi * kChunkThreads, 1u + gi};
+  const uint32_t sa = ((smem_u32(smem_raw) + 1023u) & ~1023u) + gi * kGemmSmem;
   if (threadIdx.x == 0) {
-    mbar_init(smem_u32(&mbar), 1);
+    for (uint32_t k = 0; k < kGroups; k++) mbar_init(smem_u32(&mbar[k]), 1);
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -238,14 +254,14 @@ __global__ void __launch_bounds__(kChunkThreads, 4) k_batch(BatchDev B) {
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = tmem_base;
+  const uint32_t tmem = tmem_base + gi * (kBatchTmemCols / kGroups);
   uint32_t mphase = 0;
 
   for (;;) {
-    if (threadIdx.x == 0) action = pop(B, &cur);
-    __syncthreads();
-    if (action != 1) break;
-    const Item it = cur;
+    if (g.t() == 0) action[gi] = pop(B, &cur[gi]);
+    g.sync();
+    if (action[gi] != 1) break;
+    const Item it = cur[gi];
     const sg_job& job = B.jobs[it.job];
     char* base = B.pool + B.offset[it.job];
     const bool keep = B.keep != nullptr;
@@ -258,9 +274,9 @@ __global__ void __launch_bounds__(kChunkThreads, 4) k_batch(BatchDev B) {
       float* b = a + n;
       float* c = b + n;
       const int vec = (n & 3) == 0;            // b and c 16-byte aligned (the grant is)
-      if (digest) digest_chunk((const uint32_t*)a, n, B.keep + it.job, it.chunk);
-      else if (it.phase == 0) gen_triad_chunk(b, c, n, stream_key(job.key, 1), stream_key(job.key, 2), vec, it.chunk);
-      else triad_chunk(a, b, c, 3.0f, n, vec, it.chunk);
+      if (digest) digest_chunk(g, (const uint32_t*)a, n, B.keep + it.job, it.chunk);
+      else if (it.phase == 0) gen_triad_chunk(g, b, c, n, stream_key(job.key, 1), stream_key(job.key, 2), vec, it.chunk);
+      else triad_chunk(g, a, b, c, 3.0f, n, vec, it.chunk);
     } else if (job.kind == SG_KIND_GEMM) {
       const uint32_t m = (uint32_t)job.p0, n = (uint32_t)job.p1, k = job.p2;
       const GemmLayoutHD L = gemm_layout_hd(m, n, k);
@@ -268,15 +284,17 @@ __global__ void __launch_bounds__(kChunkThreads, 4) k_batch(BatchDev B) {
       uint16_t* Bt = (uint16_t*)(base + L.B);
       float* C = (float*)(base + L.C);
       if (digest) {
-        digest_chunk((const uint32_t*)C, (uint64_t)m * n, B.keep + it.job, it.chunk);
+        digest_chunk(g, (const uint32_t*)C, (uint64_t)m * n, B.keep + it.job, it.chunk);
       } else if (it.phase == 0) {
         const uint64_t ca = cdiv((uint64_t)m * k, kBf16Chunk);
-        if (it.chunk < ca) gen_bf16_chunk(A, (uint64_t)m * k, stream_key(job.key, 1), it.chunk);
-        else gen_bf16_chunk(Bt, (uint64_t)n * k, stream_key(job.key, 2), it.chunk - ca);
+        if (it.chunk < ca) gen_bf16_chunk(g, A, (uint64_t)m * k, stream_key(job.key, 1), it.chunk);
+        else gen_bf16_chunk(g, Bt, (uint64_t)n * k, stream_key(job.key, 2), it.chunk - ca);
       } else if (gemm_bn_small(n) == 128) {
-        ok = gemm_chunk<128>(A, Bt, C, m, n, k, it.chunk, sa, tmem, smem_u32(&mbar), mphase, &s_abort);
+        ok = gemm_chunk<128>(g, A, Bt, C, m, n, k, it.chunk, sa, tmem, smem_u32(&mbar[gi]), mphase, &s_abort,
+                             &vote[gi]);
       } else {
-        ok = gemm_chunk<64>(A, Bt, C, m, n, k, it.chunk, sa, tmem, smem_u32(&mbar), mphase, &s_abort);
+        ok = gemm_chunk<64>(g, A, Bt, C, m, n, k, it.chunk, sa, tmem, smem_u32(&mbar[gi]), mphase, &s_abort,
+                            &vote[gi]);
       }
     } else {
       const uint64_t rows = job.p0, cap = job.p1;
@@ -284,67 +302,67 @@ __global__ void __launch_bounds__(kChunkThreads, 4) k_batch(BatchDev B) {
       uint64_t* scan = (uint64_t*)(base + L.scan);
       const uint64_t lk = stream_key(job.key, 1);
       if ((it.phase == 0 && it.chunk < L.nchunks) || it.phase == 2) {
-        if (threadIdx.x < 64) T[threadIdx.x] = B.tables[64ull * job.p2 + threadIdx.x];
-        __syncthreads();
+        if (g.t() < 64) T[gi][g.t()] = B.tables[64ull * job.p2 + g.t()];
+        g.sync();
       }
       if (digest) {
-        digest_chunk((const uint32_t*)(base + L.y), rows, B.keep + it.job, it.chunk);
+        digest_chunk(g, (const uint32_t*)(base + L.y), rows, B.keep + it.job, it.chunk);
       } else if (it.phase == 0) {
-        if (it.chunk < L.nchunks) spmv_chunk_sum(T, lk, rows, scan, it.chunk, red);
-        else spmv_fill_chunk((int32_t*)(base + L.col), (float*)(base + L.val), (float*)(base + L.x), cap, rows,
+        if (it.chunk < L.nchunks) spmv_chunk_sum(g, T[gi], lk, rows, scan, it.chunk, red[gi]);
+        else spmv_fill_chunk(g, (int32_t*)(base + L.col), (float*)(base + L.val), (float*)(base + L.x), cap, rows,
                              stream_key(job.key, 2), stream_key(job.key, 3), stream_key(job.key, 4),
                              it.chunk - L.nchunks);
       } else if (it.phase == 1) {
-        spmv_scan(scan, L.nchunks, red, &carry);
+        spmv_scan(g, scan, L.nchunks, red[gi], &carry[gi]);
       } else if (it.phase == 2) {
         if (L.ptr64)
-          spmv_row_ptr_chunk<int64_t>(T, lk, rows, scan, L.nchunks, (int64_t*)(base + L.row_ptr), cap, B.err,
-                                      it.chunk, red);
+          spmv_row_ptr_chunk<SubGroup, int64_t>(g, T[gi], lk, rows, scan, L.nchunks, (int64_t*)(base + L.row_ptr),
+                                                cap, B.err, it.chunk, red[gi]);
         else
-          spmv_row_ptr_chunk<int32_t>(T, lk, rows, scan, L.nchunks, (int32_t*)(base + L.row_ptr), cap, B.err,
-                                      it.chunk, red);
+          spmv_row_ptr_chunk<SubGroup, int32_t>(g, T[gi], lk, rows, scan, L.nchunks, (int32_t*)(base + L.row_ptr),
+                                                cap, B.err, it.chunk, red[gi]);
       } else {
         if (L.ptr64)
-          spmv_chunk<int64_t>((const int64_t*)(base + L.row_ptr), (const int32_t*)(base + L.col),
-                              (const float*)(base + L.val), (const float*)(base + L.x), (float*)(base + L.y), rows,
-                              1, it.chunk);
+          spmv_chunk<SubGroup, int64_t>(g, (const int64_t*)(base + L.row_ptr), (const int32_t*)(base + L.col),
+                                        (const float*)(base + L.val), (const float*)(base + L.x),
+                                        (float*)(base + L.y), rows, 1, it.chunk);
         else
-          spmv_chunk<int32_t>((const int32_t*)(base + L.row_ptr), (const int32_t*)(base + L.col),
-                              (const float*)(base + L.val), (const float*)(base + L.x), (float*)(base + L.y), rows,
-                              1, it.chunk);
+          spmv_chunk<SubGroup, int32_t>(g, (const int32_t*)(base + L.row_ptr), (const int32_t*)(base + L.col),
+                                        (const float*)(base + L.val), (const float*)(base + L.x),
+                                        (float*)(base + L.y), rows, 1, it.chunk);
       }
     }
     if (!ok) {
-      if (threadIdx.x == 0) atomicOr(B.err, 64u);
+      if (g.t() == 0) atomicOr(B.err, 64u);
       break;
     }
-    // completion: the block that finishes a phase enqueues the next one; the
+    // completion: the worker that finishes a phase enqueues the next one; the
     // one that finishes a job frees its memory for the jobs waiting on it
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    g.sync();
+    if (g.t() == 0) {
       __threadfence();
-      s_last = atomicSub(B.left + it.job, 1u) == 1u;
+      s_last[gi] = atomicSub(B.left + it.job, 1u) == 1u;
     }
-    __syncthreads();
-    if (s_last) {
+    g.sync();
+    if (s_last[gi]) {
       __threadfence();
       if (it.phase + 1 < nph) {
-        if (threadIdx.x == 0) push_phase(B, it.job, it.phase + 1);
+        if (g.t() == 0) push_phase(B, it.job, it.phase + 1);
       } else {
-        for (uint64_t e = B.succ_ptr[it.job] + threadIdx.x; e < B.succ_ptr[it.job + 1]; e += kChunkThreads) {
-          const uint32_t s = B.succ[e];
-          if (atomicSub(B.dep + s, 1u) == 1u) push_phase(B, s, 0);
+        for (uint64_t e = B.succ_ptr[it.job] + g.t(); e < B.succ_ptr[it.job + 1]; e += kChunkThreads) {
+          const uint32_t s2 = B.succ[e];
+          if (atomicSub(B.dep + s2, 1u) == 1u) push_phase(B, s2, 0);
         }
-        if (threadIdx.x == 0) atomicAdd(&B.ctr[2], 1ull);
+        if (g.t() == 0) atomicAdd(&B.ctr[2], 1ull);
       }
     }
-    __syncthreads();
+    g.sync();
   }
   tc_fence_before();
   __syncthreads();
   if (threadIdx.x < 32) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBatchTmemCols)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kBatchTmemCols)
                  : "memory");
   }
 }
@@ -436,20 +454,18 @@ extern "C" int sg_batch_build(void* dev_pool, uint64_t pool_bytes, const sg_job*
   // the largest shared-memory split, so four blocks (and their TMEM) fit an SM
   okc &= cudaFuncSetAttribute(k_batch, cudaFuncAttributePreferredSharedMemoryCarveout,
                               (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess;
-  okc &= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kChunkThreads, kBatchSmem) == cudaSuccess;
+  okc &= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kBatchThreads, kBatchSmem) == cudaSuccess;
   if (!okc) {
     cudaFree(b->dev);
     delete b;
     return SG_ERR_CUDA;
   }
-  // The kernel's registers and shared memory admit at most 4 blocks per SM,
-  // exactly what TMEM allows (4 x 128 columns); the launch steps down if the
-  // cooperative launch reports that the grid does not fit.
-  per_sm = 4;
+  // one block (four workers) per SM: a kernel that allocates TMEM gets one
+  per_sm = 1;
   b->n = n;
   b->granted = (uint32_t)pd.order.size();
   b->grid = per_sm * num_sms();
-  if ((uint64_t)b->grid > total && total > 0) b->grid = (int)total;
+  if ((uint64_t)b->grid * kGroups > total && total > 0) b->grid = (int)((total + kGroups - 1) / kGroups);
   BatchDev& B = b->d;
   B.jobs = (const sg_job*)(d + o_jobs);
   B.offset = (const uint64_t*)(d + o_off);
@@ -501,14 +517,9 @@ extern "C" int sg_batch_launch(sg_batch* b, void* stream) {
   k_batch_seed<<<256, 256, 0, st>>>(b->d.seq, b->init_items, b->d.total, b->d.ctr, b->d.err);
   if (cudaGetLastError() != cudaSuccess) return SG_ERR_CUDA;
   void* args[] = {(void*)&b->d};
-  for (;;) {
-    const cudaError_t e =
-        cudaLaunchCooperativeKernel((const void*)k_batch, dim3(b->grid), dim3(kChunkThreads), args, kBatchSmem, st);
-    if (e == cudaSuccess) return SG_OK;
-    if (e != cudaErrorCooperativeLaunchTooLarge || b->grid <= num_sms()) return SG_ERR_CUDA;
-    cudaGetLastError();
-    b->grid -= num_sms();                     // one block fewer per SM
-  }
+  const cudaError_t e =
+      cudaLaunchCooperativeKernel((const void*)k_batch, dim3(b->grid), dim3(kBatchThreads), args, kBatchSmem, st);
+  return e == cudaSuccess ? SG_OK : SG_ERR_CUDA;
 }
 
 extern "C" int sg_batch_status(sg_batch* b, uint64_t* jobs_done, uint32_t* err_flags) {
@@ -527,7 +538,7 @@ extern "C" int sg_batch_info(const sg_batch* b, uint64_t* jobs, uint64_t* chunks
   if (!b) return SG_ERR_INVALID;
   if (jobs) *jobs = b->granted;
   if (chunks) *chunks = b->d.total;
-  if (blocks) *blocks = (uint64_t)b->grid;
+  if (blocks) *blocks = (uint64_t)b->grid * kGroups;   // workers
   return SG_OK;
 }
 

@@ -41,14 +41,14 @@ __global__ void __launch_bounds__(kChunkThreads) k_triad(float* __restrict__ a, 
                                                          const float* __restrict__ c, float s, uint64_t n,
                                                          int vec, RelHook hook) {
   const uint64_t nch = (n + kTriadChunk - 1) / kTriadChunk;
-  for (uint64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) triad_chunk(a, b, c, s, n, vec, ch);
+  for (uint64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) triad_chunk(BlockGroup{}, a, b, c, s, n, vec, ch);
   job_epilogue(hook);
 }
 
 __global__ void __launch_bounds__(kChunkThreads) k_gen_triad(float* __restrict__ b, float* __restrict__ c,
                                                              uint64_t n, uint64_t kb, uint64_t kc, int vec) {
   const uint64_t nch = (n + kTriadChunk - 1) / kTriadChunk;
-  for (uint64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) gen_triad_chunk(b, c, n, kb, kc, vec, ch);
+  for (uint64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) gen_triad_chunk(BlockGroup{}, b, c, n, kb, kc, vec, ch);
 }
 
 template <typename PtrT>
@@ -58,7 +58,8 @@ __global__ void __launch_bounds__(kChunkThreads, 6) k_spmv(const PtrT* __restric
                                                            const float* __restrict__ x, float* __restrict__ y,
                                                            uint64_t rows, int vec, RelHook hook) {
   const uint64_t nch = (rows + kSpmvRowsChunk - 1) / kSpmvRowsChunk;
-  for (uint64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) spmv_chunk<PtrT>(row_ptr, col, val, x, y, rows, vec, ch);
+  for (uint64_t ch = blockIdx.x; ch < nch; ch += gridDim.x)
+    spmv_chunk<BlockGroup, PtrT>(BlockGroup{}, row_ptr, col, val, x, y, rows, vec, ch);
   job_epilogue(hook);
 }
 
@@ -69,13 +70,13 @@ __global__ void __launch_bounds__(kChunkThreads) k_spmv_chunk_sums(const uint64_
   __shared__ uint64_t red[kChunkThreads / 32];
   if (threadIdx.x < 64) T[threadIdx.x] = table[threadIdx.x];
   __syncthreads();
-  for (uint64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) spmv_chunk_sum(T, len_key, rows, scan, ch, red);
+  for (uint64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) spmv_chunk_sum(BlockGroup{}, T, len_key, rows, scan, ch, red);
 }
 
 __global__ void __launch_bounds__(kChunkThreads) k_spmv_scan_chunks(uint64_t* __restrict__ scan, uint64_t n) {
   __shared__ uint64_t wsum[kChunkThreads / 32 + 1];
   __shared__ uint64_t carry;
-  spmv_scan(scan, n, wsum, &carry);
+  spmv_scan(BlockGroup{}, scan, n, wsum, &carry);
 }
 
 template <typename PtrT>
@@ -89,7 +90,7 @@ __global__ void __launch_bounds__(kChunkThreads) k_spmv_row_ptr(const uint64_t* 
   if (threadIdx.x < 64) T[threadIdx.x] = table[threadIdx.x];
   __syncthreads();
   for (uint64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x)
-    spmv_row_ptr_chunk<PtrT>(T, len_key, rows, scan, nchunks, row_ptr, cap, err, ch, wsum);
+    spmv_row_ptr_chunk<BlockGroup, PtrT>(BlockGroup{}, T, len_key, rows, scan, nchunks, row_ptr, cap, err, ch, wsum);
 }
 
 __global__ void __launch_bounds__(kChunkThreads) k_spmv_fill(int32_t* __restrict__ col, float* __restrict__ val,
@@ -98,19 +99,20 @@ __global__ void __launch_bounds__(kChunkThreads) k_spmv_fill(int32_t* __restrict
                                                              uint64_t kv, uint64_t kx) {
   const uint64_t nnz = *total < cap ? *total : cap;
   const uint64_t nch = spmv_fill_chunks(cap, rows);
-  for (uint64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) spmv_fill_chunk(col, val, x, nnz, rows, kc, kv, kx, ch);
+  for (uint64_t ch = blockIdx.x; ch < nch; ch += gridDim.x)
+    spmv_fill_chunk(BlockGroup{}, col, val, x, nnz, rows, kc, kv, kx, ch);
 }
 
 __global__ void __launch_bounds__(kChunkThreads) k_gen_bf16(uint16_t* __restrict__ out, uint64_t count,
                                                             uint64_t key) {
   const uint64_t nch = (count + kBf16Chunk - 1) / kBf16Chunk;
-  for (uint64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) gen_bf16_chunk(out, count, key, ch);
+  for (uint64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) gen_bf16_chunk(BlockGroup{}, out, count, key, ch);
 }
 
 __global__ void __launch_bounds__(kChunkThreads) k_digest(const uint32_t* __restrict__ w, uint64_t n,
                                                           uint64_t* out, RelHook hook) {
   const uint64_t nch = (n + kDigestChunk - 1) / kDigestChunk;
-  for (uint64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) digest_chunk(w, n, out, ch);
+  for (uint64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) digest_chunk(BlockGroup{}, w, n, out, ch);
   job_epilogue(hook);
 }
 

@@ -16,6 +16,22 @@ constexpr uint64_t kFillChunk = 4096;        // non-zeros per generator chunk
 constexpr uint64_t kRowsPerScanChunk = 4096; // rows per scan chunk of the CSR build
 constexpr uint64_t kDigestChunk = 4096;      // words per digest chunk
 
+// The threads that work on one chunk: a whole block of kChunkThreads, or one
+// kChunkThreads-wide quarter of a larger block with its own named barrier.
+struct BlockGroup {
+  __device__ __forceinline__ uint32_t t() const { return threadIdx.x; }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+
+struct SubGroup {
+  uint32_t base;     // first thread of the group in the block
+  uint32_t bar;      // named barrier id (1..15)
+  __device__ __forceinline__ uint32_t t() const { return threadIdx.x - base; }
+  __device__ __forceinline__ void sync() const {
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"((uint32_t)kChunkThreads) : "memory");
+  }
+};
+
 // ----------------------------------------------------------- job layouts
 // Where each array of a job lives inside its grant (each 256-byte aligned).
 struct SpmvLayoutHD {
@@ -56,7 +72,8 @@ __host__ __device__ inline GemmLayoutHD gemm_layout_hd(uint64_t m, uint64_t n, u
 // ------------------------------------------------------------------ triad
 // a = b + s*c, product and sum rounded separately (STREAM); 128-bit when
 // the three arrays are 16-byte aligned.
-__device__ __forceinline__ void triad_chunk(float* __restrict__ a, const float* __restrict__ b,
+template <class G>
+__device__ __forceinline__ void triad_chunk(const G& g, float* __restrict__ a, const float* __restrict__ b,
                                             const float* __restrict__ c, float s, uint64_t n, int vec,
                                             uint64_t chunk) {
   const uint64_t e0 = chunk * kTriadChunk;
@@ -68,8 +85,8 @@ __device__ __forceinline__ void triad_chunk(float* __restrict__ a, const float* 
     float4 x[4], y[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-      x[k] = __ldcs(b4 + threadIdx.x + k * kChunkThreads);
-      y[k] = __ldcs(c4 + threadIdx.x + k * kChunkThreads);
+      x[k] = __ldcs(b4 + g.t() + k * kChunkThreads);
+      y[k] = __ldcs(c4 + g.t() + k * kChunkThreads);
     }
 #pragma unroll
     for (int k = 0; k < 4; k++) {
@@ -78,21 +95,22 @@ __device__ __forceinline__ void triad_chunk(float* __restrict__ a, const float* 
       r.y = __fadd_rn(x[k].y, __fmul_rn(s, y[k].y));
       r.z = __fadd_rn(x[k].z, __fmul_rn(s, y[k].z));
       r.w = __fadd_rn(x[k].w, __fmul_rn(s, y[k].w));
-      __stcs(a4 + threadIdx.x + k * kChunkThreads, r);
+      __stcs(a4 + g.t() + k * kChunkThreads, r);
     }
   } else {
-    for (uint64_t i = e0 + threadIdx.x; i < e1; i += kChunkThreads) a[i] = __fadd_rn(b[i], __fmul_rn(s, c[i]));
+    for (uint64_t i = e0 + g.t(); i < e1; i += kChunkThreads) a[i] = __fadd_rn(b[i], __fmul_rn(s, c[i]));
   }
 }
 
-__device__ __forceinline__ void gen_triad_chunk(float* __restrict__ b, float* __restrict__ c, uint64_t n,
+template <class G>
+__device__ __forceinline__ void gen_triad_chunk(const G& g, float* __restrict__ b, float* __restrict__ c, uint64_t n,
                                                 uint64_t kb, uint64_t kc, int vec, uint64_t chunk) {
   const uint64_t e0 = chunk * kTriadChunk;
   const uint64_t e1 = e0 + kTriadChunk < n ? e0 + kTriadChunk : n;
   if (vec && e1 - e0 == kTriadChunk) {
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-      const uint64_t i = (e0 >> 2) + threadIdx.x + k * kChunkThreads;
+      const uint64_t i = (e0 >> 2) + g.t() + k * kChunkThreads;
       const uint64_t e = i << 2;
       float4 vb, vc;
       vb.x = uniform_pm1(sm64_at(kb, e)); vb.y = uniform_pm1(sm64_at(kb, e + 1));
@@ -103,7 +121,7 @@ __device__ __forceinline__ void gen_triad_chunk(float* __restrict__ b, float* __
       reinterpret_cast<float4*>(c)[i] = vc;
     }
   } else {
-    for (uint64_t i = e0 + threadIdx.x; i < e1; i += kChunkThreads) {
+    for (uint64_t i = e0 + g.t(); i < e1; i += kChunkThreads) {
       b[i] = uniform_pm1(sm64_at(kb, i));
       c[i] = uniform_pm1(sm64_at(kc, i));
     }
@@ -112,11 +130,12 @@ __device__ __forceinline__ void gen_triad_chunk(float* __restrict__ b, float* __
 
 // ------------------------------------------------------------ bf16 inputs
 // eight bf16 per thread per step (one 16-byte store); `out` 16-byte aligned
-__device__ __forceinline__ void gen_bf16_chunk(uint16_t* __restrict__ out, uint64_t count, uint64_t key,
+template <class G>
+__device__ __forceinline__ void gen_bf16_chunk(const G& g, uint16_t* __restrict__ out, uint64_t count, uint64_t key,
                                                uint64_t chunk) {
   const uint64_t e0 = chunk * kBf16Chunk;
   const uint64_t e1 = e0 + kBf16Chunk < count ? e0 + kBf16Chunk : count;
-  for (uint64_t e = e0 + 8 * threadIdx.x; e < e1; e += 8 * kChunkThreads) {
+  for (uint64_t e = e0 + 8 * g.t(); e < e1; e += 8 * kChunkThreads) {
     if (e + 8 <= e1) {
       uint32_t w[4];
 #pragma unroll
@@ -164,12 +183,12 @@ __device__ __forceinline__ float spmv_fma4(const float* __restrict__ x, Idx v, I
   return acc;
 }
 
-template <typename PtrT>
-__device__ __forceinline__ void spmv_chunk(const PtrT* __restrict__ row_ptr, const int32_t* __restrict__ col,
+template <class G, typename PtrT>
+__device__ __forceinline__ void spmv_chunk(const G& g, const PtrT* __restrict__ row_ptr, const int32_t* __restrict__ col,
                                            const float* __restrict__ val, const float* __restrict__ x,
                                            float* __restrict__ y, uint64_t rows, int vec, uint64_t chunk) {
   using Idx = PtrT;
-  const uint32_t lane = threadIdx.x & 31u, sub = lane & 3u, warp = threadIdx.x >> 5;
+  const uint32_t lane = g.t() & 31u, sub = lane & 3u, warp = g.t() >> 5;
   const Idx nnz = row_ptr[rows];
   const Idx nnz4 = nnz & ~(Idx)3;  // vectors wholly inside the arrays
   const uint64_t r_end = (chunk + 1) * kSpmvRowsChunk < rows ? (chunk + 1) * kSpmvRowsChunk : rows;
@@ -212,39 +231,42 @@ __device__ __forceinline__ uint32_t row_len(const uint64_t* T, uint64_t len_key,
 }
 
 // block-wide sum of a uint64 per thread (all threads get the result)
-__device__ __forceinline__ uint64_t block_sum_u64(uint64_t v, uint64_t* red /* [kChunkThreads/32] */) {
+template <class G>
+__device__ __forceinline__ uint64_t block_sum_u64(const G& g, uint64_t v, uint64_t* red /* [kChunkThreads/32] */) {
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(SG_FULL, v, o);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
+  g.sync();
+  if ((g.t() & 31) == 0) red[g.t() >> 5] = v;
+  g.sync();
   uint64_t t = 0;
   for (int w = 0; w < kChunkThreads / 32; w++) t += red[w];
-  __syncthreads();
+  g.sync();
   return t;
 }
 
 // sum of the row lengths of scan chunk `chunk` -> scan[chunk]; T in shared memory
-__device__ __forceinline__ void spmv_chunk_sum(const uint64_t* T, uint64_t len_key, uint64_t rows,
+template <class G>
+__device__ __forceinline__ void spmv_chunk_sum(const G& g, const uint64_t* T, uint64_t len_key, uint64_t rows,
                                                uint64_t* __restrict__ scan, uint64_t chunk, uint64_t* red) {
   const uint64_t r0 = chunk * kRowsPerScanChunk;
   uint64_t sum = 0;
-  for (uint32_t k = threadIdx.x; k < kRowsPerScanChunk; k += kChunkThreads) {
+  for (uint32_t k = g.t(); k < kRowsPerScanChunk; k += kChunkThreads) {
     uint64_t r = r0 + k;
     if (r < rows) sum += row_len(T, len_key, r);
   }
-  sum = block_sum_u64(sum, red);
-  if (threadIdx.x == 0) scan[chunk] = sum;
+  sum = block_sum_u64(g, sum, red);
+  if (g.t() == 0) scan[chunk] = sum;
 }
 
 // exclusive scan of scan[0..n) in place, total at scan[n] (one block)
-__device__ __forceinline__ void spmv_scan(uint64_t* __restrict__ scan, uint64_t n, uint64_t* wsum,
+template <class G>
+__device__ __forceinline__ void spmv_scan(const G& g, uint64_t* __restrict__ scan, uint64_t n, uint64_t* wsum,
                                           uint64_t* carry) {
-  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t lane = g.t() & 31, w = g.t() >> 5;
   constexpr uint32_t nw = kChunkThreads / 32;
-  if (threadIdx.x == 0) *carry = 0;
-  __syncthreads();
+  if (g.t() == 0) *carry = 0;
+  g.sync();
   for (uint64_t base = 0; base < n; base += kChunkThreads) {
-    const uint64_t i = base + threadIdx.x;
+    const uint64_t i = base + g.t();
     const uint64_t v = i < n ? scan[i] : 0;
     uint64_t incl = v;
     for (int o = 1; o < 32; o <<= 1) {
@@ -252,8 +274,8 @@ __device__ __forceinline__ void spmv_scan(uint64_t* __restrict__ scan, uint64_t 
       if (lane >= (uint32_t)o) incl += t;
     }
     if (lane == 31) wsum[w] = incl;
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    g.sync();
+    if (g.t() == 0) {
       uint64_t run = 0;
       for (uint32_t k = 0; k < nw; k++) {
         uint64_t t = wsum[k];
@@ -262,24 +284,24 @@ __device__ __forceinline__ void spmv_scan(uint64_t* __restrict__ scan, uint64_t 
       }
       wsum[nw] = run;
     }
-    __syncthreads();
+    g.sync();
     const uint64_t c = *carry;
     if (i < n) scan[i] = c + wsum[w] + incl - v;
-    __syncthreads();
-    if (threadIdx.x == 0) *carry = c + wsum[nw];
-    __syncthreads();
+    g.sync();
+    if (g.t() == 0) *carry = c + wsum[nw];
+    g.sync();
   }
-  if (threadIdx.x == 0) scan[n] = *carry;
+  if (g.t() == 0) scan[n] = *carry;
 }
 
 // row_ptr of the rows of scan chunk `chunk` (16 consecutive rows per thread)
-template <typename PtrT>
-__device__ __forceinline__ void spmv_row_ptr_chunk(const uint64_t* T, uint64_t len_key, uint64_t rows,
+template <class G, typename PtrT>
+__device__ __forceinline__ void spmv_row_ptr_chunk(const G& g, const uint64_t* T, uint64_t len_key, uint64_t rows,
                                                    const uint64_t* __restrict__ scan, uint64_t nchunks,
                                                    PtrT* __restrict__ row_ptr, uint64_t cap, uint32_t* err,
                                                    uint64_t chunk, uint64_t* wsum) {
   constexpr int kPer = kRowsPerScanChunk / kChunkThreads;
-  const uint64_t r0 = chunk * kRowsPerScanChunk + (uint64_t)threadIdx.x * kPer;
+  const uint64_t r0 = chunk * kRowsPerScanChunk + (uint64_t)g.t() * kPer;
   uint32_t len[kPer];
   uint64_t mine = 0;
 #pragma unroll
@@ -287,15 +309,15 @@ __device__ __forceinline__ void spmv_row_ptr_chunk(const uint64_t* T, uint64_t l
     len[k] = (r0 + k < rows) ? row_len(T, len_key, r0 + k) : 0u;
     mine += len[k];
   }
-  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t lane = g.t() & 31, w = g.t() >> 5;
   uint64_t incl = mine;
   for (int o = 1; o < 32; o <<= 1) {
     uint64_t t = __shfl_up_sync(SG_FULL, incl, o);
     if (lane >= (uint32_t)o) incl += t;
   }
-  __syncthreads();
+  g.sync();
   if (lane == 31) wsum[w] = incl;
-  __syncthreads();
+  g.sync();
   uint64_t woff = 0;
   for (uint32_t k = 0; k < w; k++) woff += wsum[k];
   uint64_t pos = scan[chunk] + woff + incl - mine;
@@ -304,7 +326,7 @@ __device__ __forceinline__ void spmv_row_ptr_chunk(const uint64_t* T, uint64_t l
     if (r0 + k < rows) row_ptr[r0 + k] = (PtrT)(pos < cap ? pos : cap);  // clamp keeps reads in bounds
     pos += len[k];
   }
-  if (chunk == 0 && threadIdx.x == 0) {
+  if (chunk == 0 && g.t() == 0) {
     uint64_t total = scan[nchunks];
     row_ptr[rows] = (PtrT)(total < cap ? total : cap);
     if (total > cap && err) atomicOr(err, ERR_NNZ);   // more non-zeros than declared room
@@ -317,12 +339,13 @@ __device__ __forceinline__ void spmv_row_ptr_chunk(const uint64_t* T, uint64_t l
 // 16-byte stores. Chunk c covers non-zeros [c*kFillChunk, ...) and rows
 // [c*kFillChunk/4, ...) of x, so ceil(max(nnz, 4 rows) / kFillChunk) chunks
 // cover both.
-__device__ __forceinline__ void spmv_fill_chunk(int32_t* __restrict__ col, float* __restrict__ val,
+template <class G>
+__device__ __forceinline__ void spmv_fill_chunk(const G& g, int32_t* __restrict__ col, float* __restrict__ val,
                                                 float* __restrict__ x, uint64_t nnz, uint64_t rows,
                                                 uint64_t kc, uint64_t kv, uint64_t kx, uint64_t chunk) {
   const uint64_t e0 = chunk * kFillChunk;
   const uint64_t e1 = e0 + kFillChunk < nnz ? e0 + kFillChunk : nnz;
-  for (uint64_t e = e0 + 4 * threadIdx.x; e < e1; e += 4 * kChunkThreads) {
+  for (uint64_t e = e0 + 4 * g.t(); e < e1; e += 4 * kChunkThreads) {
     if (e + 4 <= e1) {
       const uint64_t m = e >> 1;
       const uint64_t hc0 = sm64_at(kc, m), hc1 = sm64_at(kc, m + 1);
@@ -342,7 +365,7 @@ __device__ __forceinline__ void spmv_fill_chunk(int32_t* __restrict__ col, float
   }
   const uint64_t x0 = chunk * (kFillChunk / 4);
   const uint64_t x1 = x0 + kFillChunk / 4 < rows ? x0 + kFillChunk / 4 : rows;
-  for (uint64_t r = x0 + threadIdx.x; r < x1; r += kChunkThreads) x[r] = uniform_pm1(sm64_at(kx, r));
+  for (uint64_t r = x0 + g.t(); r < x1; r += kChunkThreads) x[r] = uniform_pm1(sm64_at(kx, r));
 }
 
 __device__ __forceinline__ uint64_t spmv_fill_chunks(uint64_t nnz_cap, uint64_t rows) {
@@ -352,14 +375,15 @@ __device__ __forceinline__ uint64_t spmv_fill_chunks(uint64_t nnz_cap, uint64_t 
 
 // ----------------------------------------------------------------- digest
 // adds sum of mix64((i << 32) | w[i]) over the chunk into *out
-__device__ __forceinline__ void digest_chunk(const uint32_t* __restrict__ w, uint64_t n, uint64_t* out,
+template <class G>
+__device__ __forceinline__ void digest_chunk(const G& g, const uint32_t* __restrict__ w, uint64_t n, uint64_t* out,
                                              uint64_t chunk) {
   const uint64_t e0 = chunk * kDigestChunk;
   const uint64_t e1 = e0 + kDigestChunk < n ? e0 + kDigestChunk : n;
   uint64_t s = 0;
-  for (uint64_t i = e0 + threadIdx.x; i < e1; i += kChunkThreads) s += mix64((i << 32) | (uint64_t)w[i]);
+  for (uint64_t i = e0 + g.t(); i < e1; i += kChunkThreads) s += mix64((i << 32) | (uint64_t)w[i]);
   for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(SG_FULL, s, o);
-  if ((threadIdx.x & 31) == 0 && s) atomicAdd(reinterpret_cast<unsigned long long*>(out), (unsigned long long)s);
+  if ((g.t() & 31) == 0 && s) atomicAdd(reinterpret_cast<unsigned long long*>(out), (unsigned long long)s);
 }
 
 }  // namespace sg
