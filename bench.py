@@ -381,6 +381,63 @@ def serving_section(torch, abi, runtime, requests: int, rates=(1000, 2000, 5000,
     return out
 
 
+# ------------------------------------------------------ paper experiments
+def lifecycle_section(torch, abi, runtime, reps: int = 200) -> dict:
+    """Per-stage cost of the life cycle through the C ABI (the paper's
+    overhead comparison of init / pre-allocation / post-free / shutdown):
+    median microseconds per call, host clock, device synchronised."""
+    pool = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
+    t_init, t_decl, t_rel, t_shut = [], [], [], []
+    for i in range(max(5, reps // 20)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx = abi.sg_init(pool.data_ptr(), pool.numel(), "first_fit", 0, 4096, 4, 0)
+        t_init.append(time.perf_counter() - t0)
+        for _ in range(reps // 10):
+            t0 = time.perf_counter()
+            tk = abi.sg_declare(ctx, 1 << 20, 0)
+            rc, g = abi.sg_wait(ctx, tk, 10 ** 9)
+            t_decl.append(time.perf_counter() - t0)
+            assert rc == abi.SG_OK
+            t0 = time.perf_counter()
+            assert abi.sg_release(ctx, tk, 0, 0) == abi.SG_OK
+            torch.cuda.synchronize()
+            t_rel.append(time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        abi.sg_shutdown(ctx)
+        t_shut.append(time.perf_counter() - t0)
+    med = lambda v: 1e6 * statistics.median(v)  # noqa: E731
+    return {"init_us": med(t_init), "pre_allocation_us": med(t_decl), "post_free_us": med(t_rel),
+            "shutdown_us": med(t_shut), "note": "declare + wait for the grant; release + device sync"}
+
+
+def policies_section(torch, abi, runtime, prioritised=tg.KIND_SPMV) -> dict:
+    """The four notification policies on the mixed trace (arrivals at t=0),
+    one job kind prioritised (priority 0, the rest 1), as in the paper's
+    workload experiment with one application prioritised."""
+    tr = tg.trace_c2(saturated=True)
+    jobs = tr.jobs.copy()
+    jobs["prio"] = np.where(jobs["kind"] == prioritised, 0, 1)
+    pool = torch.empty(tr.budget, dtype=torch.uint8, device="cuda")
+    d_jobs, d_tab = runtime.to_device(jobs), runtime.device_tables(tr)
+    out = {"prioritised": tg.KIND_NAMES[prioritised]}
+    for pol in ("fifo", "first_fit", "prio_fifo", "prio_first_fit"):
+        s = runtime.Scheduler(tr.budget, pol, pool=pool)
+        s.run_trace(d_jobs, d_tab, abi.SG_RUN_SATURATED)
+        rc, log, _, st = s.run_trace(d_jobs, d_tab, abi.SG_RUN_SATURATED)
+        assert rc == abi.SG_OK
+        rec = runtime.records(log)
+        s.shutdown()
+        pr = jobs["kind"] == prioritised
+        wait = (rec["grant_t"].astype(np.int64) - rec["arrival_t"].astype(np.int64)) / 1e6
+        out[pol] = {"makespan_ms": st["makespan_ns"] / 1e6,
+                    "wait_mean_ms_prioritised": float(wait[pr].mean()),
+                    "wait_mean_ms_others": float(wait[~pr].mean())}
+    del pool
+    torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
@@ -492,6 +549,8 @@ def main():
         del sched
         torch.cuda.empty_cache()
         if not args.no_extras:
+            extra["lifecycle"] = lifecycle_section(torch, abi, runtime)
+            extra["policies"] = policies_section(torch, abi, runtime)
             extra["batching"] = batching_section(torch, abi, runtime)
             extra["serving"] = serving_section(torch, abi, runtime, args.serving_requests)
         kr = kernel_roofline(torch, abi, peaks)
