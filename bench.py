@@ -438,6 +438,58 @@ def policies_section(torch, abi, runtime, prioritised=tg.KIND_SPMV) -> dict:
     return out
 
 
+def engine_section(torch, abi, runtime) -> dict:
+    """Decision rate of the device engine alone: the replay of the 10,000-job
+    batch and of the 100,000-request serving trace (one warp, logical clock)."""
+    out = {}
+    for name, tr, pol in (("tiny10k", tg.trace_c4(), "first_fit"),
+                          ("serve100k_20000rps", tg.trace_c5(rate_per_s=20000.0), "first_fit")):
+        n = len(tr)
+        d_jobs = runtime.to_device(tr.jobs)
+        d_log = torch.empty(n * abi.RECORD_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        ws = torch.empty(abi.sg_replay_workspace_bytes(n), dtype=torch.uint8, device="cuda")
+        st = torch.zeros(4, dtype=torch.int64, device="cuda")
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        abi.sg_replay(d_jobs.data_ptr(), n, tr.budget, 256, pol, 0, False, d_log.data_ptr(), ws.data_ptr(),
+                      st.data_ptr(), stream.cuda_stream)
+        e0.record(stream)
+        abi.sg_replay(d_jobs.data_ptr(), n, tr.budget, 256, pol, 0, False, d_log.data_ptr(), ws.data_ptr(),
+                      st.data_ptr(), stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        passes = int(st[2].item())
+        events = 2 * n   # every job arrives and completes
+        out[name] = {"jobs": n, "ms": ms, "events_per_s": events / (ms * 1e-3), "us_per_event": 1e3 * ms / events,
+                     "passes": passes, "err": int(st[3].item())}
+    return out
+
+
+def mixed_plan_section(torch, abi, runtime, reps: int = 3) -> dict:
+    """The mixed trace (t=0) run as one CUDA graph on the engine's replay plan:
+    no host round trip and no admission at run time."""
+    tr = tg.trace_c2(saturated=True)
+    pool = torch.empty(tr.budget, dtype=torch.uint8, device="cuda")
+    pl = runtime.Planned(pool, tr.jobs, runtime.device_tables(tr), "first_fit", budget=tr.budget)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pl.run_graph()
+    torch.cuda.synchronize()
+    t = []
+    for _ in range(reps):
+        e0.record(stream)
+        pl.run_graph()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t.append(e0.elapsed_time(e1))
+    pl.close()
+    del pool
+    torch.cuda.empty_cache()
+    ms = statistics.median(t)
+    return {"cuda_graph_ms": ms, "jobs_per_s": len(tr) / (ms * 1e-3)}
+
+
 # ---------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
@@ -551,6 +603,8 @@ def main():
         if not args.no_extras:
             extra["lifecycle"] = lifecycle_section(torch, abi, runtime)
             extra["policies"] = policies_section(torch, abi, runtime)
+            extra["engine"] = engine_section(torch, abi, runtime)
+            extra["mixed_plan_graph"] = mixed_plan_section(torch, abi, runtime)
             extra["batching"] = batching_section(torch, abi, runtime)
             extra["serving"] = serving_section(torch, abi, runtime, args.serving_requests)
         kr = kernel_roofline(torch, abi, peaks)
