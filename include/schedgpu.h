@@ -132,9 +132,9 @@ typedef struct sg_run_stats {
  * whose engine state -- budget, used bytes, per-ticket grants, the wait
  * queue and the free-extent list: the shared data of Sec. III-B -- lives in
  * device memory allocated here, once. dev_pool: device pointer, 256-byte
- * aligned, pool_bytes long, owned by the caller. cfg may be NULL for
- * defaults. *out receives the context. Errors: SG_ERR_INVALID
- * (null/misaligned pool, bad config), SG_ERR_CUDA. */
+ * aligned, pool_bytes long (at most 2^47 granules), owned by the caller.
+ * cfg may be NULL for defaults. *out receives the context. Errors:
+ * SG_ERR_INVALID (null/misaligned/oversized pool, bad config), SG_ERR_CUDA. */
 int sg_init(sg_ctx** out, void* dev_pool, uint64_t pool_bytes, const sg_config* cfg);
 
 /* Shutdown (Sec. IV): waits for the context's streams, releases every
@@ -147,11 +147,13 @@ int sg_shutdown(sg_ctx* ctx);
 int sg_reset(sg_ctx* ctx);
 
 /* Pre-allocation, first half (Sec. IV, preCudaMalloc): declare a need of
- * `need` bytes with `priority`; the device engine queues the request and
+ * `need` bytes with `priority` (-32768..32767, smaller = served first
+ * under the priority policies); the device engine queues the request and
  * runs the admission pass. A grant never notifies other waiters.
  * Returns SG_OK with *out set (the request may already be granted; check
  * with sg_try), SG_ERR_TOO_LARGE at once if the need exceeds the pool,
- * SG_ERR_CAPACITY if the ticket table is full. */
+ * SG_ERR_CAPACITY if the ticket table is full, SG_ERR_INVALID for a
+ * priority out of range. */
 int sg_declare(sg_ctx* ctx, uint64_t need, int32_t priority, sg_ticket* out);
 
 /* Non-blocking check (Sec. IV: a non-blocking pre-allocation returns
@@ -194,7 +196,9 @@ int sg_run_trace(sg_ctx* ctx, const sg_job* jobs, uint32_t n, const uint64_t* ta
  * for bit. jobs_dev sorted by arrival_ns (ties by index); log_dev receives n
  * records; workspace_dev of sg_replay_workspace_bytes(n) bytes, owned by
  * the caller. One warp runs the whole event loop on `stream`. stats_dev:
- * 4 uint64 (peak_used, frag_waits, passes, error flags) or NULL. */
+ * 4 uint64 (peak_used, frag_waits, passes, error flags) or NULL.
+ * SG_ERR_INVALID for a null pointer, a bad policy or granule, or a budget
+ * above 2^47 granules. */
 uint64_t sg_replay_workspace_bytes(uint32_t n);
 int sg_replay(const sg_job* jobs_dev, uint32_t n, uint64_t budget, uint64_t granule,
               uint32_t policy, uint32_t flags, uint32_t exclusive, sg_record* log_dev,

@@ -66,9 +66,10 @@ __global__ void k_eng_reset(Eng E, uint64_t budget, uint64_t granule, uint32_t p
 
 // Declare tickets [first, first + count): their needs come from `jobs`
 // (ticket i = job i) or, for a single ticket, from (need, prio).
-__global__ void k_declare(Eng E, uint32_t first, uint32_t count, const sg_job* jobs, uint64_t need,
+__global__ void k_declare(Eng shared, uint32_t first, uint32_t count, const sg_job* jobs, uint64_t need,
                           int32_t prio, uint32_t exclusive) {
   if (threadIdx.x >= 32) return;
+  const Eng E = eng_live(shared);
   for (uint32_t t = first; t < first + count; t++) {
     if (!eng_lock(E)) return;
     Sess s = sess_load(E);
@@ -93,8 +94,9 @@ __global__ void k_release(Eng E, uint32_t t, uint64_t bytes) {
   eng_release_locked(E, t, bytes);
 }
 
-__global__ void k_cancel(Eng E, uint32_t t) {
+__global__ void k_cancel(Eng shared, uint32_t t) {
   if (threadIdx.x >= 32) return;
+  const Eng E = eng_live(shared);
   if (!eng_lock(E)) return;
   Sess s = sess_load(E);
   op_cancel(E, s, t, globaltimer_ns(), nullptr, nullptr);
@@ -105,9 +107,10 @@ __global__ void k_cancel(Eng E, uint32_t t) {
 // Replay: the whole event loop of a trace on one warp, logical clock.
 // Events at equal time: completions, then arrivals, then timeouts, then by
 // ticket id (the same total order as the oracle).
-__global__ void k_replay(Eng E, const sg_job* __restrict__ jobs, uint32_t n, uint32_t exclusive,
+__global__ void k_replay(Eng state, const sg_job* __restrict__ jobs, uint32_t n, uint32_t exclusive,
                          uint64_t* dur, uint64_t* tmo, EvHeap H, uint64_t* stats) {
   if (threadIdx.x >= 32) return;
+  const Eng E = eng_owned(state);   // this warp is the only user of the state
   const uint32_t lane = lane_id();
   const EngHdr* h0 = E.hdr;
   const uint64_t budget = h0->budget, granule = h0->granule;
@@ -160,7 +163,7 @@ __global__ void k_replay(Eng E, const sg_job* __restrict__ jobs, uint32_t n, uin
 
 // ------------------------------------------------------- device layout
 struct DevLayout {
-  uint64_t hdr, need_g, need_raw, prio, status, blk_done, q, qa, qt, qpos, ext_off, ext_len, rec, extra, total;
+  uint64_t hdr, need_g, need_raw, prio, status, blk_done, qa, qt, qpos, ext_off, ext_len, rec, extra, total;
   uint32_t qcap;
   uint64_t qt_len;
 };
@@ -194,7 +197,6 @@ DevLayout dev_layout(uint32_t cap, bool with_rec, uint64_t extra_bytes) {
   L.prio = o; o += a256(4ull * cap);
   L.status = o; o += a256(4ull * cap);
   L.blk_done = o; o += a256(4ull * cap);
-  L.q = o; o += a256(4ull * (cap + 1));
   L.qa = o; o += a256(4ull * L.qcap);
   L.qt = o; o += a256(8ull * L.qt_len);
   L.qpos = o; o += a256(4ull * cap);
@@ -215,7 +217,6 @@ Eng eng_from(char* base, const DevLayout& L) {
   E.prio = (int32_t*)(base + L.prio);
   E.status = (uint32_t*)(base + L.status);
   E.blk_done = (uint32_t*)(base + L.blk_done);
-  E.q = (uint32_t*)(base + L.q);
   E.qa = (uint32_t*)(base + L.qa);
   E.qt = (uint64_t*)(base + L.qt);
   E.qpos = (uint32_t*)(base + L.qpos);
@@ -321,6 +322,7 @@ extern "C" int sg_init(sg_ctx** out, void* dev_pool, uint64_t pool_bytes, const 
   uint64_t granule = d.granule ? d.granule : 256;
   if (granule < 256 || (granule & (granule - 1))) return SG_ERR_INVALID;
   if (!dev_pool || ((uintptr_t)dev_pool % 256) || pool_bytes < granule) return SG_ERR_INVALID;
+  if (pool_bytes / granule > kKeyNeedMask) return SG_ERR_INVALID;   // queue keys hold 47-bit needs
   uint32_t cap = d.max_tickets ? d.max_tickets : (1u << 17);
   if (cap > (1u << 24)) return SG_ERR_INVALID;
   sg_ctx* c = new sg_ctx();
@@ -394,6 +396,7 @@ extern "C" uint32_t sg_device_error(sg_ctx* c) { return c ? c->h_hdr[1] : 0u; }
 
 extern "C" int sg_declare(sg_ctx* c, uint64_t need, int32_t priority, sg_ticket* out) {
   if (!c || !out) return SG_ERR_INVALID;
+  if (priority < -32768 || priority > 32767) return SG_ERR_INVALID;
   uint64_t g = (need + c->granule - 1) / c->granule * c->granule;
   if (g > c->budget) return SG_ERR_TOO_LARGE;
   std::lock_guard<std::mutex> lk(c->mu);
@@ -673,6 +676,7 @@ extern "C" int sg_replay(const sg_job* jobs_dev, uint32_t n, uint64_t budget, ui
   if (!jobs_dev || !log_dev || !workspace_dev || policy > SG_POLICY_PRIO_FIRST_FIT) return SG_ERR_INVALID;
   if (granule == 0) granule = 256;
   if (granule & (granule - 1)) return SG_ERR_INVALID;
+  if (budget / granule > kKeyNeedMask) return SG_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   uint32_t cap = n;
   uint64_t extra = 16ull * cap + 16ull * (2ull * cap + 1);

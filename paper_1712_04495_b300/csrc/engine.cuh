@@ -19,6 +19,12 @@
 // coalesced; a request (rounded up to the granule) goes to the lowest
 // address extent that holds it. A request is served only if it fits the
 // byte count (budget - used) and can be placed.
+//
+// State accesses: a live engine is shared by kernels on many SMs and every
+// access goes through L2 (ld/st .cg). A replay owns its state in one warp for
+// the whole kernel, so it uses plain (L1-cached) accesses; `Eng::owned` says
+// which, and kernels set it in a local copy so the choice is made at compile
+// time.
 #pragma once
 #include "common.cuh"
 
@@ -42,7 +48,6 @@ struct Eng {               // array pointers (kernel parameter, by value)
   int32_t* prio;           // [cap]
   uint32_t* status;        // [cap]
   uint32_t* blk_done;      // [cap] finished blocks of a ticket's final kernel
-  uint32_t* q;             // [cap] waiting tickets in service order (priority policies)
   uint32_t* qa;            // [qcap] FIFO / first fit: ticket at each queue position, or kNone
   uint64_t* qt;            // 32-ary min-tree over the positions' needs (levels stored back to back)
   uint32_t* qpos;          // [cap] queue position of a waiting ticket
@@ -53,7 +58,19 @@ struct Eng {               // array pointers (kernel parameter, by value)
   sg_record* pub_rec;      // [cap] host-mapped copy of the log, or null
   uint32_t* pub_ring;      // [cap] host-mapped ring of granted tickets, or null
   uint32_t* pub_hdr;       // host-mapped: [0] ring tail, [1] error flags, [2] done count
+  uint32_t owned;          // 1: one warp owns the state for the whole kernel (replay)
 };
+
+__device__ __forceinline__ Eng eng_live(Eng E) { E.owned = 0; return E; }
+__device__ __forceinline__ Eng eng_owned(Eng E) { E.owned = 1; return E; }
+
+template <typename T>
+__device__ __forceinline__ T eld(const Eng& E, const T* p) { return E.owned ? *p : ldcg(p); }
+template <typename T>
+__device__ __forceinline__ void est(const Eng& E, T* p, T v) {
+  if (E.owned) *p = v;
+  else stcg(p, v);
+}
 
 // Lane-uniform register copy of the scalar state for one locked session.
 struct Sess {
@@ -74,23 +91,23 @@ struct EvHeap {
 __device__ __forceinline__ Sess sess_load(const Eng& E) {
   Sess s;
   const EngHdr* h = E.hdr;
-  s.budget = ldcg(&h->budget);
-  s.granule = ldcg(&h->granule);
-  s.used = ldcg(&h->used);
-  s.seq = ldcg(&h->seq);
-  s.peak = ldcg(&h->peak_used);
-  s.frag = ldcg(&h->frag_waits);
-  s.passes = ldcg(&h->passes);
-  s.policy = ldcg(&h->policy);
-  s.flags = ldcg(&h->flags);
-  s.cap = ldcg(&h->cap);
-  s.n_ext = ldcg(&h->n_ext);
-  s.q_len = ldcg(&h->q_len);
-  s.ring_tail = ldcg(&h->ring_tail);
-  s.n_done = ldcg(&h->n_done);
-  s.q_begin = ldcg(&h->q_begin);
-  s.q_end = ldcg(&h->q_end);
-  s.max_ext = ldcg(&h->max_ext);
+  s.budget = eld(E, &h->budget);
+  s.granule = eld(E, &h->granule);
+  s.used = eld(E, &h->used);
+  s.seq = eld(E, &h->seq);
+  s.peak = eld(E, &h->peak_used);
+  s.frag = eld(E, &h->frag_waits);
+  s.passes = eld(E, &h->passes);
+  s.policy = eld(E, &h->policy);
+  s.flags = eld(E, &h->flags);
+  s.cap = eld(E, &h->cap);
+  s.n_ext = eld(E, &h->n_ext);
+  s.q_len = eld(E, &h->q_len);
+  s.ring_tail = eld(E, &h->ring_tail);
+  s.n_done = eld(E, &h->n_done);
+  s.q_begin = eld(E, &h->q_begin);
+  s.q_end = eld(E, &h->q_end);
+  s.max_ext = eld(E, &h->max_ext);
   s.err = 0;
   return s;
 }
@@ -99,18 +116,18 @@ __device__ __forceinline__ void sess_store(const Eng& E, const Sess& s) {
   __syncwarp();
   if (lane_id() == 0) {
     EngHdr* h = E.hdr;
-    stcg(&h->used, s.used);
-    stcg(&h->seq, s.seq);
-    stcg(&h->peak_used, s.peak);
-    stcg(&h->frag_waits, s.frag);
-    stcg(&h->passes, s.passes);
-    stcg(&h->n_ext, s.n_ext);
-    stcg(&h->q_len, s.q_len);
-    stcg(&h->ring_tail, s.ring_tail);
-    stcg(&h->n_done, s.n_done);
-    stcg(&h->q_begin, s.q_begin);
-    stcg(&h->q_end, s.q_end);
-    stcg(&h->max_ext, s.max_ext);
+    est(E, &h->used, s.used);
+    est(E, &h->seq, s.seq);
+    est(E, &h->peak_used, s.peak);
+    est(E, &h->frag_waits, s.frag);
+    est(E, &h->passes, s.passes);
+    est(E, &h->n_ext, s.n_ext);
+    est(E, &h->q_len, s.q_len);
+    est(E, &h->ring_tail, s.ring_tail);
+    est(E, &h->n_done, s.n_done);
+    est(E, &h->q_begin, s.q_begin);
+    est(E, &h->q_end, s.q_end);
+    est(E, &h->max_ext, s.max_ext);
     if (s.err) {
       atomicOr(&h->err, s.err);
       if (E.pub_hdr) atomicOr_system(&E.pub_hdr[1], s.err);
@@ -167,39 +184,39 @@ __device__ __forceinline__ int64_t warp_find_first(uint32_t from, uint32_t len, 
 
 // remove element at index i from an array of length len (shift left)
 template <typename T>
-__device__ __forceinline__ void warp_remove_at(T* a, uint32_t i, uint32_t len) {
+__device__ __forceinline__ void warp_remove_at(const Eng& E, T* a, uint32_t i, uint32_t len) {
   for (uint32_t base = i; base + 1 < len; base += 32) {
     uint32_t k = base + lane_id();
     T v{};
     bool act = k + 1 < len;
-    if (act) v = ldcg(a + k + 1);
+    if (act) v = eld(E, a + k + 1);
     __syncwarp();
-    if (act) stcg(a + k, v);
+    if (act) est(E, a + k, v);
     __syncwarp();
   }
 }
 
 // insert v at index i of an array of length len (shift right)
 template <typename T>
-__device__ __forceinline__ void warp_insert_at(T* a, uint32_t i, uint32_t len, T v) {
+__device__ __forceinline__ void warp_insert_at(const Eng& E, T* a, uint32_t i, uint32_t len, T v) {
   // move a[i .. len-1] to a[i+1 .. len], top chunk first
   for (int64_t top = (int64_t)len; top > (int64_t)i; top -= 32) {
     int64_t k = top - (int64_t)lane_id();   // destination index
     bool act = k > (int64_t)i;
     T x{};
-    if (act) x = ldcg(a + k - 1);
+    if (act) x = eld(E, a + k - 1);
     __syncwarp();
-    if (act) stcg(a + k, x);
+    if (act) est(E, a + k, x);
     __syncwarp();
   }
-  if (lane_id() == 0) stcg(a + i, v);
+  if (lane_id() == 0) est(E, a + i, v);
   __syncwarp();
 }
 
 // --------------------------------------------------------------- extents
 __device__ __forceinline__ int64_t ext_find(const Eng& E, const Sess& s, uint64_t g) {
   const uint64_t* len = E.ext_len;
-  return warp_find_first(0, s.n_ext, [&](uint32_t i) { return ldcg(len + i) >= g; });
+  return warp_find_first(0, s.n_ext, [&](uint32_t i) { return eld(E, len + i) >= g; });
 }
 
 // largest free extent (warp-wide maximum over the list)
@@ -207,7 +224,7 @@ __device__ __forceinline__ uint64_t ext_max(const Eng& E, const Sess& s) {
   uint64_t m = 0;
   for (uint32_t base = 0; base < s.n_ext; base += 32) {
     const uint32_t i = base + lane_id();
-    const uint64_t v = i < s.n_ext ? ldcg(E.ext_len + i) : 0;
+    const uint64_t v = i < s.n_ext ? eld(E, E.ext_len + i) : 0;
     m = v > m ? v : m;
   }
 #pragma unroll
@@ -220,17 +237,17 @@ __device__ __forceinline__ uint64_t ext_max(const Eng& E, const Sess& s) {
 
 // take g bytes from the front of extent e
 __device__ __forceinline__ uint64_t ext_take(const Eng& E, Sess& s, uint32_t e, uint64_t g) {
-  uint64_t off = ldcg(E.ext_off + e);
-  uint64_t len = ldcg(E.ext_len + e);
+  uint64_t off = eld(E, E.ext_off + e);
+  uint64_t len = eld(E, E.ext_len + e);
   __syncwarp();
   if (len == g) {
-    warp_remove_at(E.ext_off, e, s.n_ext);
-    warp_remove_at(E.ext_len, e, s.n_ext);
+    warp_remove_at(E, E.ext_off, e, s.n_ext);
+    warp_remove_at(E, E.ext_len, e, s.n_ext);
     s.n_ext -= 1;
   } else {
     if (lane_id() == 0) {
-      stcg(E.ext_off + e, off + g);
-      stcg(E.ext_len + e, len - g);
+      est(E, E.ext_off + e, off + g);
+      est(E, E.ext_len + e, len - g);
     }
     __syncwarp();
   }
@@ -241,40 +258,40 @@ __device__ __forceinline__ uint64_t ext_take(const Eng& E, Sess& s, uint32_t e, 
 // return [off, off+g) to the free list, merging with neighbours
 __device__ __forceinline__ void ext_give(const Eng& E, Sess& s, uint64_t off, uint64_t g) {
   const uint64_t* eo = E.ext_off;
-  int64_t p = warp_find_first(0, s.n_ext, [&](uint32_t i) { return ldcg(eo + i) > off; });
+  int64_t p = warp_find_first(0, s.n_ext, [&](uint32_t i) { return eld(E, eo + i) > off; });
   uint32_t ip = p < 0 ? s.n_ext : (uint32_t)p;
   bool left = false, right = false;
   uint64_t ll = 0, rl = 0;
   if (ip > 0) {
-    uint64_t lo = ldcg(E.ext_off + ip - 1);
-    ll = ldcg(E.ext_len + ip - 1);
+    uint64_t lo = eld(E, E.ext_off + ip - 1);
+    ll = eld(E, E.ext_len + ip - 1);
     left = lo + ll == off;
   }
   if (ip < s.n_ext) {
-    uint64_t ro = ldcg(E.ext_off + ip);
-    rl = ldcg(E.ext_len + ip);
+    uint64_t ro = eld(E, E.ext_off + ip);
+    rl = eld(E, E.ext_len + ip);
     right = off + g == ro;
   }
   __syncwarp();
   uint64_t merged = g;
   if (left && right) {
     merged = ll + g + rl;
-    if (lane_id() == 0) stcg(E.ext_len + ip - 1, merged);
+    if (lane_id() == 0) est(E, E.ext_len + ip - 1, merged);
     __syncwarp();
-    warp_remove_at(E.ext_off, ip, s.n_ext);
-    warp_remove_at(E.ext_len, ip, s.n_ext);
+    warp_remove_at(E, E.ext_off, ip, s.n_ext);
+    warp_remove_at(E, E.ext_len, ip, s.n_ext);
     s.n_ext -= 1;
   } else if (left) {
     merged = ll + g;
-    if (lane_id() == 0) stcg(E.ext_len + ip - 1, merged);
+    if (lane_id() == 0) est(E, E.ext_len + ip - 1, merged);
     __syncwarp();
   } else if (right) {
     merged = rl + g;
-    if (lane_id() == 0) { stcg(E.ext_off + ip, off); stcg(E.ext_len + ip, merged); }
+    if (lane_id() == 0) { est(E, E.ext_off + ip, off); est(E, E.ext_len + ip, merged); }
     __syncwarp();
   } else {
-    warp_insert_at(E.ext_off, ip, s.n_ext, off);
-    warp_insert_at(E.ext_len, ip, s.n_ext, g);
+    warp_insert_at(E, E.ext_off, ip, s.n_ext, off);
+    warp_insert_at(E, E.ext_len, ip, s.n_ext, g);
     s.n_ext += 1;
   }
   if (merged > s.max_ext) s.max_ext = merged;
@@ -287,7 +304,7 @@ __device__ __forceinline__ sg_record rec_load(const Eng& E, uint32_t j) {
   const uint64_t* p = reinterpret_cast<const uint64_t*>(E.rec + j);
   uint64_t w[6];
 #pragma unroll
-  for (int i = 0; i < 6; i++) w[i] = ldcg(p + i);
+  for (int i = 0; i < 6; i++) w[i] = eld(E, p + i);
   sg_record r;
   memcpy(&r, w, sizeof r);
   return r;
@@ -298,7 +315,7 @@ __device__ __forceinline__ void rec_store(const Eng& E, uint32_t j, const sg_rec
   memcpy(w, &r, sizeof r);
   uint64_t* p = reinterpret_cast<uint64_t*>(E.rec + j);
 #pragma unroll
-  for (int i = 0; i < 6; i++) stcg(p + i, w[i]);
+  for (int i = 0; i < 6; i++) est(E, p + i, w[i]);
 }
 
 // Write a ticket's record to the device log and, in real runs, to the
@@ -397,7 +414,7 @@ __device__ __forceinline__ void heap_pop(EvHeap& H) {
 // heap != null (replay): push its completion at t + dur[j].
 __device__ __forceinline__ bool try_grant(const Eng& E, Sess& s, uint32_t j, uint64_t t,
                                           EvHeap* heap, const uint64_t* dur) {
-  uint64_t g = ldcg(E.need_g + j);
+  uint64_t g = eld(E, E.need_g + j);
   if (g > s.budget - s.used) return false;              // count test (Sec. III-B)
   if (g > s.max_ext) return false;                      // fits the count, no extent holds it
   int64_t e = ext_find(E, s, g);
@@ -412,8 +429,8 @@ __device__ __forceinline__ bool try_grant(const Eng& E, Sess& s, uint32_t j, uin
   r.offset = off;
   s.seq += 1;
   if (lane_id() == 0) {
-    stcg(E.status + j, (uint32_t)ST_RUNNING);
-    stcg(E.blk_done + j, 0u);
+    est(E, E.status + j, (uint32_t)ST_RUNNING);
+    est(E, E.blk_done + j, 0u);
   }
   publish_record(E, j, r);
   publish_grant_ring(E, s, j);
@@ -421,24 +438,42 @@ __device__ __forceinline__ bool try_grant(const Eng& E, Sess& s, uint32_t j, uin
   return true;
 }
 
-// ------------------------------------------------- queue: priority policies
-// The waiting queue in service order as a plain array (sorted insertion).
-__device__ __forceinline__ void q_remove(const Eng& E, Sess& s, uint32_t i) {
-  warp_remove_at(E.q, i, s.q_len);
-  s.q_len -= 1;
-}
-
 __device__ __forceinline__ bool is_prio_policy(const Sess& s) {
   return s.policy == SG_POLICY_PRIO_FIFO || s.policy == SG_POLICY_PRIO_FIRST_FIT;
 }
 
-// --------------------------------------------- queue: FIFO and first fit
-// Arrival order never changes under these policies, so every ticket gets the
-// next queue position once and keeps it; a served or withdrawn ticket leaves
-// a hole. A 32-ary tree of minimum needs over the positions answers "first
-// waiter at or after position i whose need is at most F" with one warp-wide
-// load per level, which is exactly the sequential scan of the policy
-// (entries above F fail the count test and are skipped, as in Sec. V).
+// ---------------------------------------------------------------- queue
+// Every queued ticket gets the next queue position once, in arrival order,
+// and keeps it; a served or withdrawn ticket leaves a hole. Each position
+// holds a key, and a 32-ary tree of minimum keys over the positions answers
+// "first waiter at or after position i whose key is at most K" with one
+// warp-wide load per level.
+//
+// FIFO and first fit: the key is the granule-rounded need, so the search is
+// exactly the sequential scan of the policy (entries above the free bytes
+// fail the count test and are skipped, as in Sec. V).
+//
+// Priority policies: the key is the priority class above the need in
+// granules. Serving order is (priority, arrival), and within one class it is
+// arrival order, i.e. position order. The smallest key in the tree gives the
+// highest class present, and the bound (class, need <= F) selects the waiters
+// of that class that fit F, in their service order.
+constexpr uint32_t kKeyShift = 47;                       // need in granules < 2^47
+constexpr uint64_t kKeyNeedMask = (1ull << kKeyShift) - 1;
+
+__device__ __forceinline__ uint64_t q_key(const Sess& s, uint64_t g, int32_t prio) {
+  if (!is_prio_policy(s)) return g;
+  return ((uint64_t)(uint32_t)(prio + 32768) << kKeyShift) | (g / s.granule);
+}
+
+// Key bound: waiters of class `cls` (priority policies) whose need is at most
+// `bytes`; `bytes` = kInf means any need.
+__device__ __forceinline__ uint64_t q_bound(const Sess& s, uint64_t cls, uint64_t bytes) {
+  if (!is_prio_policy(s)) return bytes == kInf ? kInf - 1 : bytes;
+  uint64_t gr = bytes == kInf ? kKeyNeedMask : bytes / s.granule;
+  if (gr > kKeyNeedMask) gr = kKeyNeedMask;
+  return (cls << kKeyShift) | gr;
+}
 __device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
@@ -450,15 +485,15 @@ __device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
 
 __device__ __forceinline__ void qt_set(const Eng& E, uint64_t pos, uint64_t v) {
   uint64_t off = 0, size = E.qcap, idx = pos;
-  if (lane_id() == 0) stcg(E.qt + idx, v);
+  if (lane_id() == 0) est(E, E.qt + idx, v);
   __syncwarp();
   while (size > 32) {
     const uint64_t block = idx & ~31ull;
-    const uint64_t m = warp_min_u64(ldcg(E.qt + off + block + lane_id()));
+    const uint64_t m = warp_min_u64(eld(E, E.qt + off + block + lane_id()));
     const uint64_t parent = idx >> 5;
     off += size;
     size >>= 5;
-    if (lane_id() == 0) stcg(E.qt + off + parent, m);
+    if (lane_id() == 0) est(E, E.qt + off + parent, m);
     __syncwarp();
     idx = parent;
   }
@@ -471,7 +506,7 @@ __device__ __forceinline__ int64_t qt_find(const Eng& E, uint64_t from, uint64_t
   for (;;) {
     if (pos >= size) return -1;
     const uint64_t block = pos & ~31ull, idx = block + lane_id();
-    const bool ok = idx >= pos && idx < size && ldcg(E.qt + off + idx) <= thr;
+    const bool ok = idx >= pos && idx < size && eld(E, E.qt + off + idx) <= thr;
     const unsigned m = __ballot_sync(SG_FULL, ok);
     if (m) { pos = block + (__ffs(m) - 1); break; }
     if (size <= 32) return -1;
@@ -485,44 +520,47 @@ __device__ __forceinline__ int64_t qt_find(const Eng& E, uint64_t from, uint64_t
     off -= size;
     level--;
     const uint64_t block = pos << 5, idx = block + lane_id();
-    const bool ok = idx < size && ldcg(E.qt + off + idx) <= thr;
+    const bool ok = idx < size && eld(E, E.qt + off + idx) <= thr;
     const unsigned m = __ballot_sync(SG_FULL, ok);
     pos = block + (__ffs(m) - 1);         // the parent's minimum guarantees a child
   }
   return (int64_t)pos;
 }
 
+// smallest key in the queue (kInf if empty): the tree's top level
+__device__ __forceinline__ uint64_t qt_min(const Eng& E) {
+  uint64_t off = 0, size = E.qcap;
+  while (size > 32) {
+    off += size;
+    size >>= 5;
+  }
+  return warp_min_u64(lane_id() < size ? eld(E, E.qt + off + lane_id()) : kInf);
+}
+
+// priority class of the first waiter in service order (queue not empty)
+__device__ __forceinline__ uint64_t q_top_class(const Eng& E) { return qt_min(E) >> kKeyShift; }
+
 __device__ __forceinline__ void qt_remove(const Eng& E, Sess& s, uint32_t pos) {
-  if (lane_id() == 0) stcg(E.qa + pos, kNone);
+  if (lane_id() == 0) est(E, E.qa + pos, kNone);
   __syncwarp();
   qt_set(E, pos, kInf);
   s.q_len -= 1;
 }
 
 __device__ __forceinline__ void q_insert(const Eng& E, Sess& s, uint32_t j) {
-  if (is_prio_policy(s)) {
-    // stable: after every waiter whose priority value is <= j's
-    int32_t pj = ldcg(E.prio + j);
-    const uint32_t* q = E.q;
-    const int32_t* pr = E.prio;
-    int64_t p = warp_find_first(0, s.q_len, [&](uint32_t i) { return ldcg(pr + ldcg(q + i)) > pj; });
-    uint32_t pos = p < 0 ? s.q_len : (uint32_t)p;
-    warp_insert_at(E.q, pos, s.q_len, j);
-  } else {
-    if (s.q_end >= E.qcap) {              // cannot happen: each ticket is queued once
-      s.err |= ERR_CAP;
-      return;
-    }
-    const uint32_t pos = s.q_end++;
-    if (lane_id() == 0) {
-      stcg(E.qa + pos, j);
-      stcg(E.qpos + j, pos);
-    }
-    __syncwarp();
-    qt_set(E, pos, ldcg(E.need_g + j));
+  if (s.q_end >= E.qcap) {                // cannot happen: each ticket is queued once
+    s.err |= ERR_CAP;
+    return;
   }
+  const uint32_t pos = s.q_end++;
+  if (lane_id() == 0) {
+    est(E, E.qa + pos, j);
+    est(E, E.qpos + j, pos);
+  }
+  __syncwarp();
+  qt_set(E, pos, q_key(s, eld(E, E.need_g + j), eld(E, E.prio + j)));
   s.q_len += 1;
-  if (lane_id() == 0) stcg(E.status + j, (uint32_t)ST_QUEUED);
+  if (lane_id() == 0) est(E, E.status + j, (uint32_t)ST_QUEUED);
   __syncwarp();
 }
 
@@ -536,7 +574,7 @@ __device__ __forceinline__ void policy_pass(const Eng& E, Sess& s, uint64_t t, E
       const int64_t h = qt_find(E, s.q_begin, kInf - 1);
       if (h < 0) break;
       s.q_begin = (uint32_t)h;
-      if (!try_grant(E, s, ldcg(E.qa + h), t, heap, dur)) break;
+      if (!try_grant(E, s, eld(E, E.qa + h), t, heap, dur)) break;
       qt_remove(E, s, (uint32_t)h);
     }
   } else if (s.policy == SG_POLICY_FIRST_FIT) {
@@ -549,32 +587,32 @@ __device__ __forceinline__ void policy_pass(const Eng& E, Sess& s, uint64_t t, E
       const uint64_t freeb = s.budget - s.used;
       const int64_t c = qt_find(E, i, freeb < s.max_ext ? freeb : s.max_ext);
       if (c < 0) break;
-      if (try_grant(E, s, ldcg(E.qa + c), t, heap, dur)) qt_remove(E, s, (uint32_t)c);
+      if (try_grant(E, s, eld(E, E.qa + c), t, heap, dur)) qt_remove(E, s, (uint32_t)c);
       i = (uint64_t)c + 1;
     }
   } else if (s.policy == SG_POLICY_PRIO_FIFO) {
-    // Policy 3: FIFO over the queue sorted by (priority, arrival)
-    const uint32_t* q = E.q;
+    // Policy 3: FIFO over the queue sorted by (priority, arrival): serve the
+    // first waiter of the highest class present while it fits
     while (s.q_len > 0) {
-      uint32_t h = ldcg(q);
-      if (!try_grant(E, s, h, t, heap, dur)) break;
-      q_remove(E, s, 0);
+      const int64_t h = qt_find(E, s.q_begin, q_bound(s, q_top_class(E), kInf));
+      if (h < 0) { s.err |= ERR_STATE; break; }          // the class is present
+      if (!try_grant(E, s, eld(E, E.qa + h), t, heap, dur)) break;
+      qt_remove(E, s, (uint32_t)h);
     }
   } else {
     // Policy 4: first fit inside the highest-priority class present; the next
     // class is considered only once this one is emptied
-    const uint32_t* q = E.q;
-    const int32_t* pr = E.prio;
     while (s.q_len > 0) {
-      int32_t p = ldcg(pr + ldcg(q));
-      uint32_t i = 0;
-      while (i < s.q_len) {
-        uint32_t j = ldcg(q + i);
-        if (ldcg(pr + j) != p) break;
-        if (try_grant(E, s, j, t, heap, dur)) q_remove(E, s, i);
-        else i += 1;
+      const uint64_t cls = q_top_class(E);
+      uint64_t i = s.q_begin;
+      for (;;) {
+        const uint64_t freeb = s.budget - s.used;
+        const int64_t c = qt_find(E, i, q_bound(s, cls, freeb < s.max_ext ? freeb : s.max_ext));
+        if (c < 0) break;
+        if (try_grant(E, s, eld(E, E.qa + c), t, heap, dur)) qt_remove(E, s, (uint32_t)c);
+        i = (uint64_t)c + 1;
       }
-      if (s.q_len > 0 && ldcg(pr + ldcg(q)) == p) break;
+      if (s.q_len > 0 && q_top_class(E) == cls) break;
     }
   }
   // A pass ends blocked by fragmentation when a waiter the policy would serve
@@ -585,21 +623,14 @@ __device__ __forceinline__ void policy_pass(const Eng& E, Sess& s, uint64_t t, E
     const uint64_t freeb = s.budget - s.used;
     const uint64_t* ng = E.need_g;
     bool blocked = false;
-    if (s.policy == SG_POLICY_FIFO) {
-      const int64_t h = qt_find(E, s.q_begin, kInf - 1);
-      blocked = h >= 0 && ldcg(E.need_g + ldcg(E.qa + h)) <= freeb;
+    if (s.policy == SG_POLICY_FIFO || s.policy == SG_POLICY_PRIO_FIFO) {
+      const uint64_t cls = s.policy == SG_POLICY_FIFO ? 0 : q_top_class(E);
+      const int64_t h = qt_find(E, s.q_begin, q_bound(s, cls, kInf));
+      blocked = h >= 0 && eld(E, ng + eld(E, E.qa + h)) <= freeb;
     } else if (s.policy == SG_POLICY_FIRST_FIT) {
       blocked = qt_find(E, s.q_begin, freeb) >= 0;
-    } else if (s.policy == SG_POLICY_PRIO_FIFO) {
-      blocked = ldcg(ng + ldcg(E.q)) <= freeb;
     } else {
-      const uint32_t* q = E.q;
-      const int32_t* pr = E.prio;
-      const int32_t p = ldcg(pr + ldcg(q));
-      blocked = warp_find_first(0, s.q_len, [&](uint32_t k) {
-                  const uint32_t j = ldcg(q + k);
-                  return ldcg(pr + j) == p && ldcg(ng + j) <= freeb;
-                }) >= 0;
+      blocked = qt_find(E, s.q_begin, q_bound(s, q_top_class(E), freeb)) >= 0;
     }
     if (blocked) s.frag += 1;
   }
@@ -614,11 +645,11 @@ __device__ __forceinline__ void op_declare(const Eng& E, Sess& s, uint32_t j, ui
   sg_record r;
   r.status = ST_PENDING; r.slot = slot; r.grant_seq = -1; r.grant_t = 0; r.offset = 0;
   r.done_t = 0; r.arrival_t = t;
-  uint64_t g = ldcg(E.need_g + j);
+  uint64_t g = eld(E, E.need_g + j);
   if (g > s.budget) {
     // larger than the whole pool: refused at once, never queued
     r.status = ST_TOO_LARGE;
-    if (lane_id() == 0) stcg(E.status + j, (uint32_t)ST_TOO_LARGE);
+    if (lane_id() == 0) est(E, E.status + j, (uint32_t)ST_TOO_LARGE);
     publish_record(E, j, r);
     s.n_done += 1;
     publish_done_count(E, s);
@@ -644,10 +675,10 @@ __device__ __forceinline__ void op_declare(const Eng& E, Sess& s, uint32_t j, ui
 // Returns false (and flags ERR_STATE) if j holds no memory.
 __device__ __forceinline__ bool op_release(const Eng& E, Sess& s, uint32_t j, uint64_t bytes,
                                            uint64_t t, EvHeap* heap, const uint64_t* dur) {
-  uint32_t st = ldcg(E.status + j);
+  uint32_t st = eld(E, E.status + j);
   if (st != ST_RUNNING) { s.err |= ERR_STATE; return false; }
-  uint64_t g = ldcg(E.need_g + j);
-  uint64_t raw = ldcg(E.need_raw + j);
+  uint64_t g = eld(E, E.need_g + j);
+  uint64_t raw = eld(E, E.need_raw + j);
   sg_record r = rec_load(E, j);
   uint64_t freed_off, freed;
   bool all = bytes == 0 || bytes >= raw;
@@ -656,7 +687,7 @@ __device__ __forceinline__ bool op_release(const Eng& E, Sess& s, uint32_t j, ui
     freed = g;
     r.status = ST_DONE;
     r.done_t = t;
-    if (lane_id() == 0) stcg(E.status + j, (uint32_t)ST_DONE);
+    if (lane_id() == 0) est(E, E.status + j, (uint32_t)ST_DONE);
     s.n_done += 1;
   } else {
     // shrink: keep the granule-rounded remainder at the front of the extent
@@ -664,7 +695,7 @@ __device__ __forceinline__ bool op_release(const Eng& E, Sess& s, uint32_t j, ui
     uint64_t keep = (keep_raw + s.granule - 1) / s.granule * s.granule;
     freed_off = r.offset + keep;
     freed = g - keep;
-    if (lane_id() == 0) { stcg(E.need_g + j, keep); stcg(E.need_raw + j, keep_raw); }
+    if (lane_id() == 0) { est(E, E.need_g + j, keep); est(E, E.need_raw + j, keep_raw); }
   }
   __syncwarp();
   if (freed > 0) {
@@ -680,20 +711,14 @@ __device__ __forceinline__ bool op_release(const Eng& E, Sess& s, uint32_t j, ui
 // Withdraw a waiting ticket (timeout). Returns its status after the call.
 __device__ __forceinline__ uint32_t op_cancel(const Eng& E, Sess& s, uint32_t j, uint64_t t,
                                               EvHeap* heap, const uint64_t* dur) {
-  uint32_t st = ldcg(E.status + j);
+  uint32_t st = eld(E, E.status + j);
   if (st != ST_QUEUED) return st;
-  if (is_prio_policy(s)) {
-    const uint32_t* q = E.q;
-    int64_t i = warp_find_first(0, s.q_len, [&](uint32_t k) { return ldcg(q + k) == j; });
-    if (i >= 0) q_remove(E, s, (uint32_t)i);
-  } else {
-    const uint32_t pos = ldcg(E.qpos + j);
-    if (pos < s.q_end && ldcg(E.qa + pos) == j) qt_remove(E, s, pos);
-  }
+  const uint32_t pos = eld(E, E.qpos + j);
+  if (pos < s.q_end && eld(E, E.qa + pos) == j) qt_remove(E, s, pos);
   sg_record r = rec_load(E, j);
   r.status = ST_TIMEOUT;
   r.done_t = t;
-  if (lane_id() == 0) stcg(E.status + j, (uint32_t)ST_TIMEOUT);
+  if (lane_id() == 0) est(E, E.status + j, (uint32_t)ST_TIMEOUT);
   s.n_done += 1;
   publish_record(E, j, r);
   publish_done_count(E, s);
@@ -703,7 +728,8 @@ __device__ __forceinline__ uint32_t op_cancel(const Eng& E, Sess& s, uint32_t j,
 }
 
 // Locked release from a job kernel's last block (warp 0 of it).
-__device__ __forceinline__ void eng_release_locked(const Eng& E, uint32_t j, uint64_t bytes) {
+__device__ __forceinline__ void eng_release_locked(const Eng& shared, uint32_t j, uint64_t bytes) {
+  const Eng E = eng_live(shared);
   if (!eng_lock(E)) return;
   Sess s = sess_load(E);
   op_release(E, s, j, bytes, globaltimer_ns(), nullptr, nullptr);

@@ -177,6 +177,9 @@ def test_priority_fifo_serves_higher_priority_first():
     assert s.try_grant(t2)[0] == abi.SG_NOT_READY
     s.release(t3)
     assert s.wait(t2, 10 ** 9)[0] == abi.SG_OK
+    for bad in (-32769, 32768):                 # priorities are 16-bit
+        with pytest.raises(abi.SgError):
+            s.declare(1024, priority=bad)
     s.shutdown()
 
 

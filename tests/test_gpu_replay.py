@@ -67,6 +67,29 @@ def test_workload_traces(policy):
             invariants.check_log(tr.jobs, out, tr.budget, policy)
 
 
+@pytest.mark.parametrize("policy", ["prio_fifo", "prio_first_fit"])
+def test_priority_workload_traces(policy):
+    """The priority policies on the workload traces: one kind prioritised
+    (mixed trace), three classes by kind (10,000 tiny jobs, memory pressure)."""
+    c2 = tg.trace_c2(saturated=True)
+    jobs = c2.jobs.copy()
+    jobs["prio"] = np.where(jobs["kind"] == tg.KIND_SPMV, 0, 1)
+    _parity(jobs, c2.budget, policy)
+    for tr in (tg.trace_c4(), tg.trace_c3()):
+        jobs = tr.jobs.copy()
+        jobs["prio"] = (jobs["kind"].astype(np.int64) * 7) % 3 - 1
+        _parity(jobs, tr.budget, policy)
+
+
+@pytest.mark.parametrize("policy", ["prio_fifo", "prio_first_fit"])
+def test_priority_extremes(policy):
+    """The whole int16 range of priorities, including both ends."""
+    for seed in range(6):
+        jobs = tg.random_admission_trace(seed, 120, 1 << 16, max_arrival=200, max_dur=60, prio_levels=3)
+        jobs["prio"] = np.array([-32768, 0, 32767])[jobs["prio"]]
+        _parity(jobs, 1 << 16, policy)
+
+
 @pytest.mark.timeout(600)
 def test_serving_trace_100k():
     tr = tg.trace_c5(rate_per_s=20000.0)
