@@ -244,7 +244,8 @@ def kernel_roofline(torch, abi, peaks):
     tf = flops / (ms * 1e-3) / 1e12
     out["gemm"] = {"bound": "tensor", "achieved": tf, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                    "frac": tf / peaks["bf16_tflops"], "traffic": profiled_traffic("gemm_tc_8192_bf16"), "ms": ms,
-                   "kernel": "k_gemm_tc<256> 8192^3 bf16", "flops_per_launch": flops}
+                   "kernel": f"k_gemm_tc {abi.gemm_tile_name(abi.sg_gemm_tile(M, N))} tile, 8192^3 bf16",
+                   "flops_per_launch": flops}
     del A, B, C
     # FP32 triad, n = 64M (768 MB per launch, larger than L2)
     n = 64 << 20
@@ -466,6 +467,34 @@ def engine_section(torch, abi, runtime) -> dict:
     return out
 
 
+def kinds_section(torch, abi, runtime, reps: int = 3) -> dict:
+    """Co-scheduled vs exclusive-serial makespan on the mixed trace's jobs of
+    one kind, of two kinds, and of all three (arrivals at t=0, first fit):
+    where co-scheduling pays on this GPU and where the kernels contend."""
+    tr = tg.trace_c2(saturated=True)
+    tab = runtime.device_tables(tr)
+    s = runtime.Scheduler(tr.budget, "first_fit")
+    out = {}
+    for kinds in ((tg.KIND_TRIAD,), (tg.KIND_SPMV,), (tg.KIND_GEMM,), (tg.KIND_TRIAD, tg.KIND_SPMV),
+                  (tg.KIND_TRIAD, tg.KIND_GEMM), (tg.KIND_SPMV, tg.KIND_GEMM),
+                  (tg.KIND_TRIAD, tg.KIND_SPMV, tg.KIND_GEMM)):
+        jobs = tr.jobs[np.isin(tr.jobs["kind"], kinds)].copy()
+        d = runtime.to_device(jobs)
+        ms = {}
+        for name, mode in (("co", abi.SG_RUN_SATURATED), ("exclusive", abi.SG_RUN_SATURATED | abi.SG_RUN_EXCLUSIVE)):
+            t = []
+            for _ in range(reps):
+                rc, _, _, st = s.run_trace(d, tab, mode)
+                assert rc == abi.SG_OK
+                t.append(st["makespan_ns"] / 1e6)
+            ms[name] = statistics.median(t)
+        out["+".join(tg.KIND_NAMES[k] for k in kinds)] = {
+            "jobs": len(jobs), "co_ms": ms["co"], "exclusive_ms": ms["exclusive"],
+            "ratio": ms["co"] / ms["exclusive"]}
+    s.shutdown()
+    return out
+
+
 def mixed_plan_section(torch, abi, runtime, reps: int = 3) -> dict:
     """The mixed trace (t=0) run as one CUDA graph on the engine's replay plan:
     no host round trip and no admission at run time."""
@@ -515,7 +544,7 @@ def main():
         ops = _torch_ops(torch.device("cuda", local))
     peaks = _peaks()
 
-    # the project's autotuner picks the GEMM tile width of every shape the
+    # the project's autotuner picks the GEMM output tile of every shape the
     # workloads use (outside any timed region)
     shapes = sorted({(s_, s_, s_) for s_ in (64, 128, 256, 512, 1024, 2048, 4096, 8192)})
     scratch = torch.empty(600 << 20, dtype=torch.uint8, device="cuda")
@@ -604,6 +633,7 @@ def main():
             extra["lifecycle"] = lifecycle_section(torch, abi, runtime)
             extra["policies"] = policies_section(torch, abi, runtime)
             extra["engine"] = engine_section(torch, abi, runtime)
+            extra["kinds"] = kinds_section(torch, abi, runtime)
             extra["mixed_plan_graph"] = mixed_plan_section(torch, abi, runtime)
             extra["batching"] = batching_section(torch, abi, runtime)
             extra["serving"] = serving_section(torch, abi, runtime, args.serving_requests)
@@ -630,7 +660,7 @@ def main():
                            "l2": "inputs larger than L2 (about 50 GB of job data per step)",
                            "parallelism": f"replicas x{ws}"},
                 "gpu_launches": launches, "clocks": clocks, "wall_s": wall,
-                "autotune_gemm_tile_n": {str(sh[0]): w for sh, w, _ in tuned}}
+                "autotune_gemm_tile": {str(sh[0]): abi.gemm_tile_name(w) for sh, w, _ in tuned}}
         line.update(extra)
         print(json.dumps(line), flush=True)
     if ws > 1:

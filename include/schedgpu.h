@@ -311,22 +311,29 @@ int sg_gen_spmv(void* base, uint64_t rows, uint64_t nnz_cap, const uint64_t* tab
 int sg_gemm_bf16(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, uint32_t N,
                  uint32_t K, void* stream);
 
-/* sg_gemm_bf16 with an explicit output-tile width: tile_n = 64, 128 or 256
- * columns per 128-row tile (0 = the built-in choice, sg_gemm_tile_n). */
-int sg_gemm_bf16_tiled(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, uint32_t N,
-                       uint32_t K, uint32_t tile_n, void* stream);
-/* The tile width sg_gemm_bf16 uses for an M x N output: the autotuner's
- * choice if it has tuned that shape, else the widest that still gives
- * every SM a tile with at most 1/8 of it wasted. Host only. */
-uint32_t sg_gemm_tile_n(uint32_t M, uint32_t N);
+/* GEMM output tiles. A tile code is (rows << 16) | columns: 128 x 64,
+ * 128 x 128, 128 x 256 and 256 x 256. The plain widths 64, 128 and 256 are
+ * accepted for the 128-row tiles. */
+#define SG_GEMM_TILE(m, n) ((((uint32_t)(m)) << 16) | (uint32_t)(n))
 
-/* Autotuner for the GEMM tile width. shapes: n_shapes (M, N, K) triples
+/* sg_gemm_bf16 with an explicit output tile (0 = sg_gemm_tile's choice).
+ * SG_ERR_INVALID for a code that is not one of the four tiles. */
+int sg_gemm_bf16_tiled(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, uint32_t N,
+                       uint32_t K, uint32_t tile, void* stream);
+/* The tile code sg_gemm_bf16 uses for an M x N output: the autotuner's
+ * choice if it has tuned that shape, else 256 x 256 when every SM gets a
+ * tile, else the widest 128-row tile that half of the SMs get (at most 1/8
+ * of a tile wasted on the edges), else 128 x 64. Host only. */
+uint32_t sg_gemm_tile(uint32_t M, uint32_t N);
+
+/* Autotuner for the GEMM output tile. shapes: n_shapes (M, N, K) triples
  * (host). For each shape, generates inputs in `scratch` (device, needs
  * 2MK + 2NK + 4MN bytes rounded to 256 B per array; shapes that do not fit
- * are skipped with chosen = 0), times every width (one warm-up, median of
- * three CUDA-event timings on `stream`) and records the fastest for (M, N)
- * in a process-wide table used by every later GEMM launch. chosen / best_ms
- * (host, n_shapes each) may be NULL. Synchronous. */
+ * are skipped with chosen = 0), times every tile that fits the shape (one
+ * warm-up, median of three CUDA-event timings on `stream`) and records the
+ * fastest tile code for (M, N) in a process-wide table used by every later
+ * GEMM launch. chosen (tile codes) / best_ms (host, n_shapes each) may be
+ * NULL. Synchronous. */
 int sg_autotune_gemm(const uint32_t* shapes, uint32_t n_shapes, void* scratch, uint64_t scratch_bytes,
                      uint32_t* chosen, float* best_ms, void* stream);
 /* Forget every tuned shape. */

@@ -96,7 +96,7 @@ _SIGS = {
     "sg_gen_spmv": ([_P, _U64, _U64, _P, _U64, _P, _P], ctypes.c_int),
     "sg_gemm_bf16": ([_P, _P, _P, _U32, _U32, _U32, _P], ctypes.c_int),
     "sg_gemm_bf16_tiled": ([_P, _P, _P, _U32, _U32, _U32, _U32, _P], ctypes.c_int),
-    "sg_gemm_tile_n": ([_U32, _U32], _U32),
+    "sg_gemm_tile": ([_U32, _U32], _U32),
     "sg_autotune_gemm": ([_P, _U32, _P, _U64, _P, _P, _P], ctypes.c_int),
     "sg_autotune_clear": ([], ctypes.c_int),
     "sg_gen_gemm": ([_P, _P, _U32, _U32, _U32, _U64, _P], ctypes.c_int),
@@ -296,16 +296,30 @@ def sg_gemm_bf16(A, Bt, C, M: int, N: int, K: int, stream: int = 0) -> int:
     return lib().sg_gemm_bf16(A, Bt, C, M, N, K, stream)
 
 
-def sg_gemm_bf16_tiled(A, Bt, C, M: int, N: int, K: int, tile_n: int, stream: int = 0) -> int:
-    return lib().sg_gemm_bf16_tiled(A, Bt, C, M, N, K, tile_n, stream)
+def gemm_tile(m: int, n: int) -> int:
+    """Tile code of an m x n output tile (SG_GEMM_TILE)."""
+    return (m << 16) | n
 
 
-def sg_gemm_tile_n(M: int, N: int) -> int:
-    return lib().sg_gemm_tile_n(M, N)
+def gemm_tile_name(code: int) -> str:
+    if 0 < code < 65536:
+        code = gemm_tile(128, code)
+    return f"{code >> 16}x{code & 0xFFFF}"
+
+
+GEMM_TILES = (gemm_tile(128, 64), gemm_tile(128, 128), gemm_tile(128, 256), gemm_tile(256, 256))
+
+
+def sg_gemm_bf16_tiled(A, Bt, C, M: int, N: int, K: int, tile: int, stream: int = 0) -> int:
+    return lib().sg_gemm_bf16_tiled(A, Bt, C, M, N, K, tile, stream)
+
+
+def sg_gemm_tile(M: int, N: int) -> int:
+    return lib().sg_gemm_tile(M, N)
 
 
 def sg_autotune_gemm(shapes, scratch_ptr: int, scratch_bytes: int, stream: int = 0):
-    """Tune the tile width of each (M, N, K); returns [(shape, width, ms)]."""
+    """Tune the output tile of each (M, N, K); returns [(shape, tile code, ms)]."""
     arr = np.ascontiguousarray(np.asarray(shapes, dtype=np.uint32).reshape(-1, 3))
     n = len(arr)
     chosen = np.zeros(n, dtype=np.uint32)

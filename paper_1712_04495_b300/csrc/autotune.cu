@@ -1,6 +1,6 @@
-// GEMM tile-width autotuner: on each shape, time every output-tile width the
-// kernel supports (64, 128, 256 columns per 128-row tile) with CUDA events
-// and remember the fastest. sg_gemm_bf16 and every job launch consult the
+// GEMM tile autotuner: on each shape, time every output tile the kernel
+// supports (128 x 64, 128 x 128, 128 x 256, 256 x 256) with CUDA events and
+// remember the fastest. sg_gemm_bf16 and every job launch consult the
 // table before falling back to the built-in choice.
 #include <algorithm>
 #include <map>
@@ -13,13 +13,13 @@
 namespace sg {
 namespace {
 std::mutex g_tune_mu;
-std::map<std::pair<uint32_t, uint32_t>, uint32_t> g_tuned;   // (M, N) -> tile width
+std::map<std::pair<uint32_t, uint32_t>, uint32_t> g_tuned;   // (M, N) -> tile code
 }  // namespace
 
-int tuned_tile_n(uint32_t M, uint32_t N) {
+uint32_t tuned_tile(uint32_t M, uint32_t N) {
   std::lock_guard<std::mutex> g(g_tune_mu);
   auto it = g_tuned.find({M, N});
-  return it == g_tuned.end() ? 0 : (int)it->second;
+  return it == g_tuned.end() ? 0 : it->second;
 }
 
 }  // namespace sg
@@ -51,14 +51,16 @@ extern "C" int sg_autotune_gemm(const uint32_t* shapes, uint32_t n_shapes, void*
     }
     float best = -1.f;
     uint32_t pick = 0;
-    for (uint32_t w : {64u, 128u, 256u}) {
-      if (w > 64 && N < w) continue;
-      if (launch_gemm_bn(A, B, C, M, N, K, (int)w, none, st) != SG_OK) { rc = SG_ERR_CUDA; break; }   // warm-up
+    for (uint32_t w : {SG_GEMM_TILE(128, 64), SG_GEMM_TILE(128, 128), SG_GEMM_TILE(128, 256),
+                       SG_GEMM_TILE(256, 256)}) {
+      const uint32_t tm = w >> 16, tn = w & 0xFFFFu;
+      if (w != SG_GEMM_TILE(128, 64) && (N < tn || M < tm)) continue;
+      if (launch_gemm_tile(A, B, C, M, N, K, w, none, st) != SG_OK) { rc = SG_ERR_CUDA; break; }   // warm-up
       const int reps = 3;
       std::vector<float> t;
       for (int r = 0; r < reps && rc == SG_OK; r++) {
         cudaEventRecord(e0, st);
-        if (launch_gemm_bn(A, B, C, M, N, K, (int)w, none, st) != SG_OK) rc = SG_ERR_CUDA;
+        if (launch_gemm_tile(A, B, C, M, N, K, w, none, st) != SG_OK) rc = SG_ERR_CUDA;
         cudaEventRecord(e1, st);
         float ms = 0.f;
         if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)

@@ -31,12 +31,15 @@ int launch_digest(const void* p, uint64_t words, uint64_t* out, const RelHook& h
 // tcgen05 GEMM (gemm.cu): C = A * Bt^T
 int launch_gemm(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, uint32_t N, uint32_t K,
                 const RelHook& h, cudaStream_t st);
-// the same with an explicit output-tile width (64, 128 or 256; 0 = heuristic)
-int launch_gemm_bn(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, uint32_t N, uint32_t K,
-                   int bn, const RelHook& h, cudaStream_t st);
-int gemm_pick_bn(uint32_t M, uint32_t N);
-// width the autotuner recorded for an M x N output, or 0 (autotune.cu)
-int tuned_tile_n(uint32_t M, uint32_t N);
+// the same with an explicit output tile (an SG_GEMM_TILE code, or 64 / 128 /
+// 256 for a 128-row tile of that width; 0 = tuned, else built-in choice)
+int launch_gemm_tile(const uint16_t* A, const uint16_t* Bt, float* C, uint32_t M, uint32_t N, uint32_t K,
+                     uint32_t tile, const RelHook& h, cudaStream_t st);
+uint32_t gemm_pick_tile(uint32_t M, uint32_t N);
+uint32_t gemm_tile_code(uint32_t tile);   // 64 / 128 / 256 -> SG_GEMM_TILE(128, n)
+bool gemm_tile_valid(uint32_t tile);
+// tile code the autotuner recorded for an M x N output, or 0 (autotune.cu)
+uint32_t tuned_tile(uint32_t M, uint32_t N);
 // driver entry point and kernel attributes, once (call before stream capture)
 int gemm_prepare();
 

@@ -1,6 +1,6 @@
 """Run one job kernel on its own, for profiling and timing.
 
-    python -m paper_1712_04495_b300.kernel_cases gemm  [M=N=K, default 8192] [launches]
+    python -m paper_1712_04495_b300.kernel_cases gemm  [M=N=K, default 8192] [launches] [tile, e.g. 256x256]
     python -m paper_1712_04495_b300.kernel_cases spmv  [rows, default 1e7]   [launches]
     python -m paper_1712_04495_b300.kernel_cases triad [n, default 64M]      [launches]
     python -m paper_1712_04495_b300.kernel_cases fill  [rows, default 1e7]   [launches]
@@ -36,7 +36,7 @@ def _time(fn, launches: int) -> float:
     return e0.elapsed_time(e1) / launches
 
 
-def run(kind: str, size: int | None = None, launches: int = 3) -> dict:
+def run(kind: str, size: int | None = None, launches: int = 3, tile: str | None = None) -> dict:
     st = torch.cuda.current_stream().cuda_stream
     if kind == "gemm":
         m = size or 8192
@@ -44,8 +44,11 @@ def run(kind: str, size: int | None = None, launches: int = 3) -> dict:
         B = torch.empty(m * m, dtype=torch.int16, device="cuda")
         C = torch.empty(m * m, dtype=torch.float32, device="cuda")
         assert abi.sg_gen_gemm(A.data_ptr(), B.data_ptr(), m, m, m, 42, st) == 0
-        ms = _time(lambda: abi.sg_gemm_bf16(A.data_ptr(), B.data_ptr(), C.data_ptr(), m, m, m, st), launches)
-        return {"kernel": "gemm", "size": m, "ms": ms, "tflops": 2.0 * m ** 3 / (ms * 1e-3) / 1e12}
+        code = abi.gemm_tile(*(int(x) for x in tile.split("x"))) if tile else abi.sg_gemm_tile(m, m)
+        ms = _time(lambda: abi.sg_gemm_bf16_tiled(A.data_ptr(), B.data_ptr(), C.data_ptr(), m, m, m, code, st),
+                   launches)
+        return {"kernel": "gemm", "tile": abi.gemm_tile_name(code), "size": m, "ms": ms,
+                "tflops": 2.0 * m ** 3 / (ms * 1e-3) / 1e12}
     if kind in ("spmv", "fill"):
         rows = size or 10_000_000
         lam = 16.0
@@ -92,4 +95,4 @@ if __name__ == "__main__":
     k = sys.argv[1]
     size = int(float(sys.argv[2])) if len(sys.argv) > 2 else None
     launches = int(sys.argv[3]) if len(sys.argv) > 3 else 3
-    print(run(k, size, launches))
+    print(run(k, size, launches, sys.argv[4] if len(sys.argv) > 4 else None))

@@ -104,16 +104,16 @@ def test_spmv_full_size_sampled():
     assert np.all(np.abs(gy - y) <= 1e-5 * mag + 1e-30)
 
 
-def _gemm(M, N, Kd, key, tile_n=None):
+def _gemm(M, N, Kd, key, tile=None):
     abi = _abi()
     A = torch.empty(M * Kd, dtype=torch.int16, device="cuda")
     Bt = torch.empty(N * Kd, dtype=torch.int16, device="cuda")
     C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
     assert abi.sg_gen_gemm(A.data_ptr(), Bt.data_ptr(), M, N, Kd, key) == 0
-    if tile_n is None:
+    if tile is None:
         assert abi.sg_gemm_bf16(A.data_ptr(), Bt.data_ptr(), C.data_ptr(), M, N, Kd) == 0
     else:
-        assert abi.sg_gemm_bf16_tiled(A.data_ptr(), Bt.data_ptr(), C.data_ptr(), M, N, Kd, tile_n) == 0
+        assert abi.sg_gemm_bf16_tiled(A.data_ptr(), Bt.data_ptr(), C.data_ptr(), M, N, Kd, tile) == 0
     torch.cuda.synchronize()
     assert abi.sg_kernel_errors() == 0
     return A, Bt, C
@@ -139,11 +139,18 @@ def test_gemm_matches_fp64(M, N, Kd):
     assert rel <= 1e-5, rel
 
 
-@pytest.mark.parametrize("tile_n", [64, 128, 256])
-@pytest.mark.parametrize("M,N,Kd", [(256, 512, 128), (300, 520, 136), (130, 70, 64)])
-def test_gemm_every_tile_width(M, N, Kd, tile_n):
-    key = 77 + M + N + Kd + tile_n
-    A, Bt, C = _gemm(M, N, Kd, key, tile_n)
+_TILES = [(128, 64), (128, 128), (128, 256), (256, 256)]
+
+
+@pytest.mark.parametrize("tile", _TILES, ids=[f"{m}x{n}" for m, n in _TILES])
+@pytest.mark.parametrize("M,N,Kd", [(256, 512, 128), (300, 520, 136), (130, 70, 64), (600, 700, 1000),
+                                    (1024, 768, 512)])
+def test_gemm_every_tile(M, N, Kd, tile):
+    """Every output tile, on shapes with ragged edges in M, N and K, several
+    tiles per CTA (1024 x 768 on 256 x 256) and more K blocks than stages."""
+    abi = _abi()
+    key = 77 + M + N + Kd + tile[0] + tile[1]
+    A, Bt, C = _gemm(M, N, Kd, key, abi.gemm_tile(*tile))
     ref = K.gemm(key, M, N, Kd)
     got = C.cpu().numpy().astype(np.float64)
     assert np.all(np.isfinite(got))
@@ -152,9 +159,16 @@ def test_gemm_every_tile_width(M, N, Kd, tile_n):
 
 def test_gemm_tile_choice():
     abi = _abi()
-    assert abi.sg_gemm_tile_n(8192, 8192) == 256
-    assert abi.sg_gemm_tile_n(2048, 2048) == 128
-    assert abi.sg_gemm_tile_n(512, 512) == 64
+    assert abi.sg_gemm_tile(8192, 8192) == abi.gemm_tile(256, 256)
+    assert abi.sg_gemm_tile(2048, 2048) == abi.gemm_tile(128, 256)
+    assert abi.sg_gemm_tile(512, 512) == abi.gemm_tile(128, 64)
+    # plain widths name the 128-row tiles; anything else is refused
+    x = torch.zeros(1 << 16, dtype=torch.float32, device="cuda")
+    p = x.data_ptr()
+    assert abi.sg_gemm_bf16_tiled(p, p, p, 128, 128, 64, 128) == abi.SG_OK
+    for bad in (32, 512, abi.gemm_tile(256, 128), abi.gemm_tile(64, 64)):
+        assert abi.sg_gemm_bf16_tiled(p, p, p, 128, 128, 64, bad) == abi.SG_ERR_INVALID
+    torch.cuda.synchronize()
 
 
 def test_gemm_full_size_sampled():
@@ -196,14 +210,14 @@ def test_autotuner_picks_a_width_and_gemm_stays_exact():
     try:
         res = abi.sg_autotune_gemm([(256, 256, 256), (512, 384, 64), (8192, 8192, 8192)], scratch.data_ptr(),
                                    scratch.numel())
-        assert res[0][1] in (64, 128, 256) and res[0][2] > 0
-        assert res[1][1] in (64, 128, 256)
+        assert res[0][1] in abi.GEMM_TILES and res[0][2] > 0
+        assert res[1][1] in abi.GEMM_TILES
         assert res[2][1] == 0                      # does not fit the scratch: skipped
-        assert abi.sg_gemm_tile_n(256, 256) == res[0][1]
+        assert abi.sg_gemm_tile(256, 256) == res[0][1]
         key = 5
         A, Bt, C = _gemm(512, 384, 64, key)       # uses the tuned width
         ref = K.gemm(key, 512, 384, 64)
         assert np.linalg.norm(C.cpu().numpy() - ref) / np.linalg.norm(ref) <= 1e-5
     finally:
         abi.sg_autotune_clear()
-    assert abi.sg_gemm_tile_n(256, 256) == 64
+    assert abi.sg_gemm_tile(256, 256) == abi.gemm_tile(128, 64)
