@@ -175,6 +175,21 @@ int sg_wait(sg_ctx* ctx, sg_ticket t, uint64_t timeout_ns, sg_grant* out);
  * paper's check that the bytes were pre-allocated). */
 int sg_release(sg_ctx* ctx, sg_ticket t, uint64_t bytes, void* stream);
 
+/* Withdraw a request that is still waiting (what an expired blocking
+ * pre-allocation does, Sec. IV): the engine removes it from the queue and
+ * re-runs the notification pass. Returns SG_ERR_TIMEOUT if it was
+ * withdrawn, SG_OK (with *out, may be NULL) if it had already been granted,
+ * SG_ERR_INVALID for an unknown ticket. Synchronous. */
+int sg_cancel(sg_ctx* ctx, sg_ticket t, sg_grant* out);
+
+/* The grant notifications of Sec. IV (the paper's signal to a waiting
+ * client): copies up to `max` tickets granted since *cursor, in grant order,
+ * into out[], advances *cursor and sets *n_out. Start with *cursor = 0
+ * after sg_init or sg_reset. Non-blocking, host only. SG_ERR_CAPACITY if
+ * more than max_tickets grants were not read in time (the ring wrapped),
+ * SG_ERR_DEVICE after a device engine error. */
+int sg_poll_grants(sg_ctx* ctx, uint32_t* cursor, sg_ticket* out, uint32_t max, uint32_t* n_out);
+
 /* Run job `job` in the memory granted to ticket t, on `stream`: its input
  * generator, then its kernel, whose last block releases the ticket
  * (wake-on-release without a host round trip). tables_dev: device array of
@@ -229,6 +244,67 @@ int sg_replay_noalloc(const sg_job* jobs_dev, uint32_t n, uint64_t budget, uint6
  * GEMM's mbarrier waits), OR-ed since the last call, then cleared.
  * Synchronous (device-wide). */
 int sg_kernel_errors(uint32_t* flags_out);
+
+/* ------------------------------------------- client processes (server) */
+/* The paper's clients are separate application processes that share the
+ * scheduler (Sec. III). Here one server process owns the pool and the
+ * device engine, and clients reach it over a UNIX socket (SOCK_SEQPACKET).
+ * The pool is mapped into each client through CUDA IPC, and clients run
+ * their own kernels on their grants.
+ *
+ * A grant is pushed to its client as soon as the engine makes it; this
+ * replaces the paper's signal. A request with a finite timeout is withdrawn
+ * when the timeout expires.
+ *
+ * Dead-client check: the server takes each client's pid from the socket.
+ * When a connection closes, the client's tickets stay held until that
+ * process has exited, because its kernels may still run until then. After
+ * that, waiting requests are withdrawn and grants released, which notifies
+ * the other waiters. A process that closes its connection but keeps running
+ * keeps its grants until it exits. */
+typedef struct sg_server sg_server;
+typedef struct sg_server_counters {
+    uint64_t clients_accepted, clients_reaped, declares, grants, timeouts, releases, protocol_errors;
+    uint32_t clients_open, tickets_open;
+} sg_server_counts;
+
+/* Serve ctx's pool at socket_path (created, replacing a stale socket file;
+ * at most 107 bytes) on a service thread. Call it from a thread whose
+ * current device is ctx's. Clients can map the pool only if it is device
+ * memory that CUDA IPC can share (a cudaMalloc allocation or part of one;
+ * otherwise sg_client_pool fails and grants carry ptr = NULL). ctx stays
+ * usable in-process. SG_ERR_INVALID if the socket cannot be bound. */
+int sg_server_start(sg_ctx* ctx, const char* socket_path, sg_server** out);
+int sg_server_counters(sg_server* s, sg_server_counts* out);
+/* Stop serving and free the server (not ctx; tickets of clients still
+ * connected stay with ctx until sg_reset / sg_shutdown). */
+int sg_server_stop(sg_server* s);
+
+typedef struct sg_client sg_client;
+/* Connect to a server. SG_ERR_UNKNOWN if it cannot be reached or stops
+ * answering (30 s), on this and every later client call. */
+int sg_client_connect(const char* socket_path, sg_client** out);
+int sg_client_info(sg_client* c, uint64_t* pool_bytes, uint64_t* granule);
+/* This process's device pointer to the pool (CUDA IPC mapping on the
+ * current device, opened on the first call). Grants returned after this
+ * call carry ptr = pool + offset. */
+int sg_client_pool(sg_client* c, void** dev_ptr);
+/* Pre-allocation request (sg_declare for a client process): the server's
+ * engine queues it; it is withdrawn after timeout_ns if still waiting
+ * (UINT64_MAX: never). */
+int sg_client_declare(sg_client* c, uint64_t need, int32_t priority, uint64_t timeout_ns, sg_ticket* out);
+/* SG_OK (granted, *out filled), SG_NOT_READY, SG_ERR_TIMEOUT (withdrawn),
+ * SG_ERR_INVALID (not this client's ticket). */
+int sg_client_try(sg_client* c, sg_ticket t, sg_grant* out);
+/* sg_client_try that blocks up to max_block_ns for the grant; SG_NOT_READY
+ * if it has not come by then. */
+int sg_client_wait(sg_client* c, sg_ticket t, uint64_t max_block_ns, sg_grant* out);
+/* Post-free (sg_release for a client): the caller's work on the grant must
+ * be complete (synchronise its streams first). bytes = 0 releases all. */
+int sg_client_release(sg_client* c, sg_ticket t, uint64_t bytes);
+/* Close the connection (tickets still held stay with the server until this
+ * process exits) and unmap the pool. */
+int sg_client_close(sg_client* c);
 
 /* ------------------------------------------------------- batching */
 /* One CUDA graph for a whole trace: a static co-schedule. plan (host, n

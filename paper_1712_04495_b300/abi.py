@@ -54,6 +54,19 @@ class SgRunStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class SgServerCounts(ctypes.Structure):
+    _fields_ = [("clients_accepted", ctypes.c_uint64), ("clients_reaped", ctypes.c_uint64),
+                ("declares", ctypes.c_uint64), ("grants", ctypes.c_uint64), ("timeouts", ctypes.c_uint64),
+                ("releases", ctypes.c_uint64), ("protocol_errors", ctypes.c_uint64),
+                ("clients_open", ctypes.c_uint32), ("tickets_open", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+NO_TIMEOUT = (1 << 64) - 1
+
+
 class SgError(RuntimeError):
     def __init__(self, code: int, what: str):
         super().__init__(f"{what}: {sg_strerror(code)} (code {code})")
@@ -101,6 +114,19 @@ _SIGS = {
     "sg_autotune_clear": ([], ctypes.c_int),
     "sg_gen_gemm": ([_P, _P, _U32, _U32, _U32, _U64, _P], ctypes.c_int),
     "sg_digest": ([_P, _U64, _P, _P], ctypes.c_int),
+    "sg_cancel": ([_P, _U32, _P], ctypes.c_int),
+    "sg_poll_grants": ([_P, _P, _P, _U32, _P], ctypes.c_int),
+    "sg_server_start": ([_P, ctypes.c_char_p, _P], ctypes.c_int),
+    "sg_server_counters": ([_P, _P], ctypes.c_int),
+    "sg_server_stop": ([_P], ctypes.c_int),
+    "sg_client_connect": ([ctypes.c_char_p, _P], ctypes.c_int),
+    "sg_client_info": ([_P, _P, _P], ctypes.c_int),
+    "sg_client_pool": ([_P, _P], ctypes.c_int),
+    "sg_client_declare": ([_P, _U64, ctypes.c_int32, _U64, _P], ctypes.c_int),
+    "sg_client_try": ([_P, _U32, _P], ctypes.c_int),
+    "sg_client_wait": ([_P, _U32, _U64, _P], ctypes.c_int),
+    "sg_client_release": ([_P, _U32, _U64], ctypes.c_int),
+    "sg_client_close": ([_P], ctypes.c_int),
 }
 
 _lib = None
@@ -175,6 +201,83 @@ def sg_wait(ctx: int, ticket: int, timeout_ns: int):
 
 def sg_release(ctx: int, ticket: int, nbytes: int = 0, stream: int = 0) -> int:
     return lib().sg_release(ctx, ticket, nbytes, stream)
+
+
+def sg_cancel(ctx: int, ticket: int):
+    """(code, grant or None): SG_ERR_TIMEOUT if withdrawn, SG_OK if it was granted first."""
+    g = SgGrant()
+    rc = lib().sg_cancel(ctx, ticket, ctypes.byref(g))
+    return rc, (g if rc == SG_OK else None)
+
+
+def sg_poll_grants(ctx: int, cursor: int, max_n: int = 1024):
+    """(code, new cursor, tickets granted since `cursor`)."""
+    cur = _U32(cursor)
+    out = np.zeros(max(1, max_n), dtype=np.uint32)
+    n = _U32()
+    rc = lib().sg_poll_grants(ctx, ctypes.byref(cur), out.ctypes.data, max_n, ctypes.byref(n))
+    return rc, cur.value, [int(x) for x in out[: n.value]]
+
+
+# ---------------------------------------------------- server and clients
+def sg_server_start(ctx: int, socket_path: str) -> int:
+    out = _P()
+    _check(lib().sg_server_start(ctx, socket_path.encode(), ctypes.byref(out)), "sg_server_start")
+    return out.value
+
+
+def sg_server_counters(srv: int) -> dict:
+    c = SgServerCounts()
+    _check(lib().sg_server_counters(srv, ctypes.byref(c)), "sg_server_counters")
+    return c.as_dict()
+
+
+def sg_server_stop(srv: int):
+    _check(lib().sg_server_stop(srv), "sg_server_stop")
+
+
+def sg_client_connect(socket_path: str) -> int:
+    out = _P()
+    _check(lib().sg_client_connect(socket_path.encode(), ctypes.byref(out)), "sg_client_connect")
+    return out.value
+
+
+def sg_client_info(cl: int):
+    pb, gr = _U64(), _U64()
+    _check(lib().sg_client_info(cl, ctypes.byref(pb), ctypes.byref(gr)), "sg_client_info")
+    return pb.value, gr.value
+
+
+def sg_client_pool(cl: int) -> int:
+    p = _P()
+    _check(lib().sg_client_pool(cl, ctypes.byref(p)), "sg_client_pool")
+    return p.value
+
+
+def sg_client_declare(cl: int, need: int, priority: int = 0, timeout_ns: int = NO_TIMEOUT) -> int:
+    t = _U32()
+    _check(lib().sg_client_declare(cl, need, priority, timeout_ns, ctypes.byref(t)), "sg_client_declare")
+    return t.value
+
+
+def sg_client_try(cl: int, ticket: int):
+    g = SgGrant()
+    rc = lib().sg_client_try(cl, ticket, ctypes.byref(g))
+    return rc, (g if rc == SG_OK else None)
+
+
+def sg_client_wait(cl: int, ticket: int, max_block_ns: int):
+    g = SgGrant()
+    rc = lib().sg_client_wait(cl, ticket, max_block_ns, ctypes.byref(g))
+    return rc, (g if rc == SG_OK else None)
+
+
+def sg_client_release(cl: int, ticket: int, nbytes: int = 0) -> int:
+    return lib().sg_client_release(cl, ticket, nbytes)
+
+
+def sg_client_close(cl: int):
+    _check(lib().sg_client_close(cl), "sg_client_close")
 
 
 def sg_launch(ctx: int, ticket: int, job: np.ndarray, tables_ptr: int = 0, stream: int = 0) -> int:

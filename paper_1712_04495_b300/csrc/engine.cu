@@ -430,6 +430,17 @@ extern "C" int sg_try(sg_ctx* c, sg_ticket t, sg_grant* out) {
   return grant_of(c, t, out);
 }
 
+// Withdraw a waiting request (re-runs the notification pass) and report the
+// ticket's state afterwards: SG_ERR_TIMEOUT if it was withdrawn, SG_OK (with
+// *out) if it had been granted first.
+static int cancel_locked(sg_ctx* c, sg_ticket t, sg_grant* out) {
+  k_cancel<<<1, 32, 0, c->ctrl>>>(c->eng, t);
+  if (cudaGetLastError() != cudaSuccess) return SG_ERR_CUDA;
+  if (cudaStreamSynchronize(c->ctrl) != cudaSuccess) return SG_ERR_CUDA;
+  int rc = grant_of(c, t, out);
+  return rc == SG_NOT_READY ? SG_ERR_DEVICE : rc;
+}
+
 extern "C" int sg_wait(sg_ctx* c, sg_ticket t, uint64_t timeout_ns, sg_grant* out) {
   if (!c || t >= c->cap) return SG_ERR_INVALID;
   uint64_t t0 = now_ns();
@@ -440,15 +451,35 @@ extern "C" int sg_wait(sg_ctx* c, sg_ticket t, uint64_t timeout_ns, sg_grant* ou
     if (now_ns() - t0 >= timeout_ns) break;
     for (int i = 0; i < 64; i++) cpu_relax();
   }
-  // expired: withdraw the request (re-runs the notification pass)
-  {
-    std::lock_guard<std::mutex> lk(c->mu);
-    k_cancel<<<1, 32, 0, c->ctrl>>>(c->eng, t);
-    if (cudaGetLastError() != cudaSuccess) return SG_ERR_CUDA;
-    if (cudaStreamSynchronize(c->ctrl) != cudaSuccess) return SG_ERR_CUDA;
-  }
-  int rc = grant_of(c, t, out);
-  return rc == SG_NOT_READY ? SG_ERR_DEVICE : rc;
+  // expired: withdraw the request
+  std::lock_guard<std::mutex> lk(c->mu);
+  return cancel_locked(c, t, out);
+}
+
+extern "C" int sg_cancel(sg_ctx* c, sg_ticket t, sg_grant* out) {
+  if (!c || t >= c->cap) return SG_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (t >= c->next_ticket) return SG_ERR_INVALID;
+  const int rc = grant_of(c, t, out);
+  if (rc != SG_NOT_READY) return rc;                  // granted, withdrawn or finished already
+  return cancel_locked(c, t, out);
+}
+
+namespace sg {
+cudaStream_t ctx_control_stream(sg_ctx* c) { return c->ctrl; }
+char* ctx_pool_base(sg_ctx* c) { return c->pool; }
+uint64_t ctx_pool_bytes(sg_ctx* c) { return c->pool_bytes; }
+uint64_t ctx_granule(sg_ctx* c) { return c->granule; }
+}  // namespace sg
+
+extern "C" int sg_poll_grants(sg_ctx* c, uint32_t* cursor, sg_ticket* out, uint32_t max, uint32_t* n_out) {
+  if (!c || !cursor || (!out && max) || !n_out) return SG_ERR_INVALID;
+  const uint32_t tail = c->h_hdr[0];
+  if (tail - *cursor > c->cap) return SG_ERR_CAPACITY;   // the ring wrapped over unread grants
+  uint32_t n = 0;
+  while (*cursor != tail && n < max) out[n++] = (sg_ticket)c->h_ring[(*cursor)++ % c->cap];
+  *n_out = n;
+  return c->h_hdr[1] ? SG_ERR_DEVICE : SG_OK;
 }
 
 extern "C" int sg_release(sg_ctx* c, sg_ticket t, uint64_t bytes, void* stream) {

@@ -43,6 +43,11 @@ uint32_t tuned_tile(uint32_t M, uint32_t N);
 // driver entry point and kernel attributes, once (call before stream capture)
 int gemm_prepare();
 
+// a context's control stream and pool (engine.cu), for the scheduler server
+cudaStream_t ctx_control_stream(sg_ctx* c);
+char* ctx_pool_base(sg_ctx* c);
+uint64_t ctx_pool_bytes(sg_ctx* c);
+uint64_t ctx_granule(sg_ctx* c);
 // generator + kernel (+ digest when keep_slot) of one job inside its grant
 int launch_job(const sg_job& job, char* base, const uint64_t* tables, const RelHook& hook,
                uint64_t* keep_slot, uint32_t* err, cudaStream_t st, uint64_t* launches);
