@@ -412,6 +412,55 @@ def lifecycle_section(torch, abi, runtime, reps: int = 200) -> dict:
             "shutdown_us": med(t_shut), "note": "declare + wait for the grant; release + device sync"}
 
 
+def _latency_client(path: str, reps: int, q) -> None:
+    """Client process of `client_server_section` (no CUDA work of its own)."""
+    sys.path.insert(0, ROOT)
+    from paper_1712_04495_b300 import abi as a
+    t0 = time.perf_counter()
+    cl = a.sg_client_connect(path)
+    t_conn = time.perf_counter() - t0
+    t_decl, t_rel = [], []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        tk = a.sg_client_declare(cl, 1 << 20, 0)
+        rc, _ = a.sg_client_wait(cl, tk, 10 ** 9)
+        t_decl.append(time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        rc2 = a.sg_client_release(cl, tk, 0)
+        t_rel.append(time.perf_counter() - t0)
+        if rc != a.SG_OK or rc2 != a.SG_OK:
+            q.put({"error": f"codes {rc} {rc2}"})
+            return
+    a.sg_client_close(cl)
+    med = lambda v: 1e6 * statistics.median(v)  # noqa: E731
+    q.put({"connect_us": 1e6 * t_conn, "pre_allocation_us": med(t_decl), "post_free_us": med(t_rel)})
+
+
+def client_server_section(torch, abi, runtime, reps: int = 300) -> dict:
+    """The same life-cycle stages from a separate client process through the
+    scheduler server (UNIX socket; grants pushed by the server): the paper's
+    comparison of the library with a client-server design."""
+    import multiprocessing as mp
+    import tempfile
+    pool = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
+    sched = runtime.Scheduler(pool.numel(), "first_fit", pool=pool, max_tickets=reps + 16)
+    path = os.path.join(tempfile.mkdtemp(prefix="sg_bench_"), "sock")
+    srv = abi.sg_server_start(sched.ctx, path)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_latency_client, args=(path, reps, q))
+    p.start()
+    try:
+        out = q.get(timeout=300)
+    finally:
+        p.join(30)
+        abi.sg_server_stop(srv)
+        sched.shutdown()
+    out["note"] = ("client process -> server: declare + wait for the pushed grant; "
+                   "release round trip (the release kernel runs after the reply)")
+    return out
+
+
 def policies_section(torch, abi, runtime, prioritised=tg.KIND_SPMV) -> dict:
     """The four notification policies on the mixed trace (arrivals at t=0),
     one job kind prioritised (priority 0, the rest 1), as in the paper's
@@ -631,6 +680,7 @@ def main():
         torch.cuda.empty_cache()
         if not args.no_extras:
             extra["lifecycle"] = lifecycle_section(torch, abi, runtime)
+            extra["client_server"] = client_server_section(torch, abi, runtime)
             extra["policies"] = policies_section(torch, abi, runtime)
             extra["engine"] = engine_section(torch, abi, runtime)
             extra["kinds"] = kinds_section(torch, abi, runtime)
