@@ -101,7 +101,7 @@ typedef struct sg_record {
 typedef struct sg_config {
     uint32_t policy;       /* SG_POLICY_*                                  */
     uint32_t flags;        /* SG_FLAG_*                                    */
-    uint32_t max_tickets;  /* capacity of the ticket table (0 = 1 << 17)   */
+    uint32_t max_tickets;  /* tickets in use at once (0 = 1 << 17, <= 1 << 24) */
     uint32_t n_streams;    /* stream slots for sg_run_trace (0 = 32)       */
     uint64_t granule;      /* allocation granule, power of two >= 256 (0 = 256) */
 } sg_config;
@@ -152,8 +152,11 @@ int sg_reset(sg_ctx* ctx);
  * runs the admission pass. A grant never notifies other waiters.
  * Returns SG_OK with *out set (the request may already be granted; check
  * with sg_try), SG_ERR_TOO_LARGE at once if the need exceeds the pool,
- * SG_ERR_CAPACITY if the ticket table is full, SG_ERR_INVALID for a
- * priority out of range. */
+ * SG_ERR_CAPACITY if max_tickets tickets are in use, SG_ERR_INVALID for a
+ * priority out of range. A ticket is in use until its full release has run
+ * on the device (sg_release with bytes = 0, or the job launched with
+ * sg_launch finishing) or its request timed out; after that a later
+ * sg_declare may hand out the same ticket number. */
 int sg_declare(sg_ctx* ctx, uint64_t need, int32_t priority, sg_ticket* out);
 
 /* Non-blocking check (Sec. IV: a non-blocking pre-allocation returns

@@ -168,9 +168,9 @@ struct DevLayout {
   uint64_t qt_len;
 };
 
-uint32_t queue_positions(uint32_t cap) {
+uint32_t queue_positions(uint32_t n) {
   uint32_t q = 32;
-  while (q < cap) q <<= 1;
+  while (q < n) q <<= 1;
   return q;
 }
 
@@ -185,10 +185,13 @@ uint64_t tree_entries(uint32_t qcap) {
   return total;
 }
 
-DevLayout dev_layout(uint32_t cap, bool with_rec, uint64_t extra_bytes) {
+// positions: queue positions (a power of two >= positions); a replay queues
+// each job at most once (positions = n), a live context recycles tickets
+// and compacts its positions (positions = 2 * cap)
+DevLayout dev_layout(uint32_t cap, bool with_rec, uint64_t extra_bytes, uint64_t positions) {
   auto a256 = [](uint64_t x) { return (x + 255) / 256 * 256; };
   DevLayout L;
-  L.qcap = queue_positions(cap);
+  L.qcap = queue_positions((uint32_t)positions);
   L.qt_len = tree_entries(L.qcap);
   uint64_t o = 0;
   L.hdr = o; o += a256(sizeof(EngHdr));
@@ -269,6 +272,8 @@ struct sg_ctx {
   std::mutex mu;
   uint32_t next_ticket = 0;
   std::vector<uint8_t> rel_enq;  // a full release is already enqueued
+  std::vector<uint32_t> free_tickets;   // finished tickets that sg_declare may reuse
+  std::vector<uint8_t> in_free;
   cudaStream_t ctrl = nullptr;
   uint32_t n_hp = 8;             // high-priority slots [n_slots, n_slots + n_hp): GEMM jobs
   std::vector<cudaStream_t> slots;
@@ -310,6 +315,8 @@ static int ctx_reset_locked(sg_ctx* c) {
   c->h_hdr[2] = 0;
   c->next_ticket = 0;
   std::fill(c->rel_enq.begin(), c->rel_enq.end(), 0);
+  c->free_tickets.clear();
+  std::fill(c->in_free.begin(), c->in_free.end(), 0);
   return SG_OK;
 }
 
@@ -335,11 +342,12 @@ extern "C" int sg_init(sg_ctx** out, void* dev_pool, uint64_t pool_bytes, const 
   c->cap = cap;
   c->n_slots = d.n_streams ? d.n_streams : 32;
   c->rel_enq.assign(cap, 0);
+  c->in_free.assign(cap, 0);
   int rc = SG_ERR_CUDA;
   do {
     if (cudaGetDevice(&c->device) != cudaSuccess) break;
     uint64_t extra = 64ull * cap + 8ull * cap + 256;  // jobs, keep, err
-    c->L = dev_layout(cap, true, extra);
+    c->L = dev_layout(cap, true, extra, 2ull * cap);
     if (cudaMalloc(&c->dev, c->L.total) != cudaSuccess) break;
     c->eng = eng_from(c->dev, c->L);
     c->d_jobs = (sg_job*)(c->dev + c->L.extra);
@@ -394,14 +402,37 @@ extern "C" int sg_reset(sg_ctx* c) {
 
 extern "C" uint32_t sg_device_error(sg_ctx* c) { return c ? c->h_hdr[1] : 0u; }
 
+// Tickets whose life is over: the full release has run on the device (it
+// was requested by sg_release or is done by the job itself), or the request
+// timed out. The device keeps no reference to them; they may be reused.
+static void collect_finished(sg_ctx* c) {
+  for (uint32_t t = 0; t < c->next_ticket; t++) {
+    if (c->in_free[t]) continue;
+    const uint32_t st = (uint32_t)c->h_rec[t].status;
+    if ((st == SG_ST_DONE && c->rel_enq[t]) || st == SG_ST_TIMEOUT) {
+      c->in_free[t] = 1;
+      c->free_tickets.push_back(t);
+    }
+  }
+}
+
 extern "C" int sg_declare(sg_ctx* c, uint64_t need, int32_t priority, sg_ticket* out) {
   if (!c || !out) return SG_ERR_INVALID;
   if (priority < -32768 || priority > 32767) return SG_ERR_INVALID;
   uint64_t g = (need + c->granule - 1) / c->granule * c->granule;
   if (g > c->budget) return SG_ERR_TOO_LARGE;
   std::lock_guard<std::mutex> lk(c->mu);
-  if (c->next_ticket >= c->cap) return SG_ERR_CAPACITY;
-  uint32_t t = c->next_ticket++;
+  uint32_t t;
+  if (c->next_ticket < c->cap) {
+    t = c->next_ticket++;
+  } else {
+    if (c->free_tickets.empty()) collect_finished(c);
+    if (c->free_tickets.empty()) return SG_ERR_CAPACITY;
+    t = c->free_tickets.back();
+    c->free_tickets.pop_back();
+    c->in_free[t] = 0;
+    c->rel_enq[t] = 0;
+  }
   c->h_rec[t].status = SG_ST_PENDING;
   k_declare<<<1, 32, 0, c->ctrl>>>(c->eng, t, 1, nullptr, need, priority, 0);
   if (cudaGetLastError() != cudaSuccess) return SG_ERR_CUDA;
@@ -697,7 +728,7 @@ extern "C" int sg_run_trace(sg_ctx* c, const sg_job* jobs, uint32_t n, const uin
 extern "C" uint64_t sg_replay_workspace_bytes(uint32_t n) {
   uint64_t cap = n ? n : 1;
   uint64_t extra = 16ull * cap + 16ull * (2 * cap + 1);   // dur, tmo, heap t/k
-  return dev_layout((uint32_t)cap, false, extra).total;
+  return dev_layout((uint32_t)cap, false, extra, cap).total;
 }
 
 extern "C" int sg_replay(const sg_job* jobs_dev, uint32_t n, uint64_t budget, uint64_t granule,
@@ -711,7 +742,7 @@ extern "C" int sg_replay(const sg_job* jobs_dev, uint32_t n, uint64_t budget, ui
   cudaStream_t st = (cudaStream_t)stream;
   uint32_t cap = n;
   uint64_t extra = 16ull * cap + 16ull * (2ull * cap + 1);
-  DevLayout L = dev_layout(cap, false, extra);
+  DevLayout L = dev_layout(cap, false, extra, cap);
   char* base = (char*)workspace_dev;
   Eng E = eng_from(base, L);
   E.rec = log_dev;

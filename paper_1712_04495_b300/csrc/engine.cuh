@@ -547,8 +547,45 @@ __device__ __forceinline__ void qt_remove(const Eng& E, Sess& s, uint32_t pos) {
   s.q_len -= 1;
 }
 
+// Positions run out when many tickets have come and gone: move the waiting
+// tickets, in order, to positions 0, 1, ... Removed positions already hold
+// kInf, so only the moved entries touch the tree. A live context has at
+// least twice as many positions as tickets, so this leaves at least half
+// free and its cost is spread over that many insertions.
+__device__ __forceinline__ void q_compact(const Eng& E, Sess& s) {
+  const uint32_t lane = lane_id();
+  uint32_t k = 0;
+  for (uint32_t base = s.q_begin; base < s.q_end; base += 32) {
+    const uint32_t p = base + lane;
+    const uint32_t t = p < s.q_end ? eld(E, E.qa + p) : kNone;
+    const uint64_t key = t != kNone ? eld(E, E.qt + p) : kInf;
+    unsigned live = __ballot_sync(SG_FULL, t != kNone);
+    __syncwarp();
+    while (live) {
+      const int src_lane = __ffs(live) - 1;
+      live &= live - 1;
+      const uint32_t from = __shfl_sync(SG_FULL, p, src_lane);
+      const uint32_t tk = __shfl_sync(SG_FULL, t, src_lane);
+      const uint64_t ky = __shfl_sync(SG_FULL, key, src_lane);
+      const uint32_t to = k++;
+      if (to == from) continue;            // already in place (warp-uniform)
+      if (lane == 0) {
+        est(E, E.qa + from, kNone);
+        est(E, E.qa + to, tk);
+        est(E, E.qpos + tk, to);
+      }
+      __syncwarp();
+      qt_set(E, from, kInf);
+      qt_set(E, to, ky);
+    }
+  }
+  s.q_begin = 0;
+  s.q_end = k;
+}
+
 __device__ __forceinline__ void q_insert(const Eng& E, Sess& s, uint32_t j) {
-  if (s.q_end >= E.qcap) {                // cannot happen: each ticket is queued once
+  if (s.q_end >= E.qcap) q_compact(E, s);
+  if (s.q_end >= E.qcap) {                // every position holds a waiting ticket
     s.err |= ERR_CAP;
     return;
   }

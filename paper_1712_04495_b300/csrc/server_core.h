@@ -202,6 +202,7 @@ class Server {
   void forget_ticket(uint32_t t) {
     auto it = tickets_.find(t);
     if (it == tickets_.end()) return;
+    if (!it->second.granted) n_waiting_--;
     auto c = clients_.find(it->second.fd);
     if (c != clients_.end()) {
       auto& v = c->second.tickets;
@@ -250,6 +251,7 @@ class Server {
         const uint64_t now = server_now_ns();
         const uint64_t dl = m.b == kNone ? kNone : (now + m.b < now ? kNone : now + m.b);
         tickets_[t] = Ticket{fd, dl, false, m.a};
+        n_waiting_++;
         if (dl < next_deadline_) next_deadline_ = dl;
         cl.tickets.push_back(t);
         publish_open_counts();
@@ -327,6 +329,7 @@ class Server {
         auto it = tickets_.find(buf[i]);
         if (it == tickets_.end() || it->second.granted) continue;
         it->second.granted = true;
+        n_waiting_--;
         bump(&ServerCounters::grants);
         auto c = clients_.find(it->second.fd);
         if (c == clients_.end() || c->second.closed) continue;   // reaped later
@@ -359,6 +362,7 @@ class Server {
       const bool live = c != clients_.end() && !c->second.closed;
       if (rc == 0) {              // granted just before the deadline
         it->second.granted = true;
+        n_waiting_--;
         bump(&ServerCounters::grants);
         if (live) {
           WireMsg m{};
@@ -412,9 +416,12 @@ class Server {
   void loop() {
     eng_->on_thread_start();
     epoll_event evs[64];
-    uint32_t idle = 0;
     while (run_) {
-      const int n = epoll_wait(epfd_, evs, 64, 0);
+      // wake at once on socket activity; otherwise poll the grant ring every
+      // few microseconds while a request waits, less often when all are held
+      const long wait_ns = n_waiting_ ? 2000 : (tickets_.empty() ? 1000000 : 50000);
+      timespec ts{0, wait_ns};
+      const int n = epoll_pwait2(epfd_, evs, 64, &ts, nullptr);
       for (int i = 0; i < n; i++) {
         const int fd = evs[i].data.fd;
         if (fd == lfd_) accept_all();
@@ -424,10 +431,6 @@ class Server {
       const uint64_t now = server_now_ns();
       expire(now);
       reap(now);
-      // poll quickly while requests are open; back off when idle
-      if (n > 0 || !tickets_.empty()) idle = 0;
-      else if (idle < 1000) idle++;
-      std::this_thread::sleep_for(std::chrono::microseconds(idle < 100 ? 20 : 500));
     }
   }
 
@@ -441,6 +444,7 @@ class Server {
   uint32_t cursor_ = 0;
   uint64_t last_reap_ = 0;
   uint64_t next_deadline_ = kNone;   // earliest deadline of a waiting request
+  uint32_t n_waiting_ = 0;           // tickets not granted yet
   std::mutex stat_mu_;
   ServerCounters cnt_{};
 };

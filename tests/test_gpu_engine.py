@@ -183,6 +183,39 @@ def test_priority_fifo_serves_higher_priority_first():
     s.shutdown()
 
 
+@pytest.mark.parametrize("policy", ["first_fit", "prio_first_fit"])
+def test_tickets_are_recycled_and_queue_positions_compacted(policy):
+    """A long-running context: far more requests than tickets (64) and queue
+    positions (128) while one large request keeps waiting; the waiters keep
+    their order across the compactions."""
+    abi, rt = _rt()
+    s = rt.Scheduler(MIB, policy, max_tickets=64)
+    hold = s.declare(600 * 1024)
+    assert s.wait(hold, 10 ** 9)[0] == abi.SG_OK
+    big = s.declare(800 * 1024)                     # waits: 424 KiB free
+    seen = set()
+    for i in range(500):
+        t = s.declare(100 * 1024)                   # first fit serves it past the waiter
+        seen.add(t)
+        assert s.wait(t, 10 ** 9)[0] == abi.SG_OK
+        assert s.release(t) == abi.SG_OK
+        torch.cuda.synchronize()
+    assert len(seen) < 64                           # ticket numbers were reused
+    assert s.try_grant(big)[0] == abi.SG_NOT_READY
+    second = s.declare(800 * 1024)                  # waits behind `big`
+    torch.cuda.synchronize()
+    assert s.try_grant(second)[0] == abi.SG_NOT_READY
+    s.release(hold)
+    rc, g = s.wait(big, 10 ** 9)
+    assert rc == abi.SG_OK and g.offset == 0
+    assert s.try_grant(second)[0] == abi.SG_NOT_READY
+    s.release(big)
+    assert s.wait(second, 10 ** 9)[0] == abi.SG_OK
+    s.release(second)
+    torch.cuda.synchronize()
+    s.shutdown()
+
+
 def test_serving_results_equal_alone_and_in_the_mix():
     # open-loop arrivals admitted while earlier requests run; every request's
     # output equals its output when it runs alone on the GPU
