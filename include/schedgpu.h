@@ -102,8 +102,10 @@ typedef struct sg_config {
     uint32_t policy;       /* SG_POLICY_*                                  */
     uint32_t flags;        /* SG_FLAG_*                                    */
     uint32_t max_tickets;  /* tickets in use at once (0 = 1 << 17, <= 1 << 24) */
-    uint32_t n_streams;    /* stream slots for sg_run_trace (0 = 32)       */
+    uint32_t n_streams;    /* stream slots for sg_run_trace's non-GEMM jobs (0 = 4) */
     uint64_t granule;      /* allocation granule, power of two >= 256 (0 = 256) */
+    uint32_t n_gemm_streams; /* high-priority slots for GEMM jobs (0 = 4)  */
+    uint32_t reserved;     /* 0 */
 } sg_config;
 
 typedef struct sg_grant {

@@ -34,7 +34,8 @@ assert RECORD_DTYPE.itemsize == 48
 class SgConfig(ctypes.Structure):
     _fields_ = [("policy", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("max_tickets", ctypes.c_uint32), ("n_streams", ctypes.c_uint32),
-                ("granule", ctypes.c_uint64)]
+                ("granule", ctypes.c_uint64), ("n_gemm_streams", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
 
 class SgGrant(ctypes.Structure):
@@ -164,9 +165,9 @@ def sg_strerror(code: int) -> str:
 
 # ------------------------------------------------------------- life cycle
 def sg_init(pool_ptr: int, pool_bytes: int, policy=0, flags=0, max_tickets=0, n_streams=0,
-            granule=0) -> int:
+            granule=0, n_gemm_streams=0) -> int:
     pol = POLICIES[policy] if isinstance(policy, str) else int(policy)
-    cfg = SgConfig(pol, flags, max_tickets, n_streams, granule)
+    cfg = SgConfig(pol, flags, max_tickets, n_streams, granule, n_gemm_streams, 0)
     out = _P()
     _check(lib().sg_init(ctypes.byref(out), pool_ptr, pool_bytes, ctypes.byref(cfg)), "sg_init")
     return out.value

@@ -55,13 +55,14 @@ class Scheduler:
     """A context over one device pool (``sg_init`` .. ``sg_shutdown``)."""
 
     def __init__(self, pool_bytes: int, policy="first_fit", flags: int = 0, max_tickets: int = 0,
-                 n_streams: int = 0, granule: int = 0, pool: torch.Tensor | None = None):
+                 n_streams: int = 0, granule: int = 0, pool: torch.Tensor | None = None,
+                 n_gemm_streams: int = 0):
         _require_cuda()
         self.pool = pool if pool is not None else torch.empty(pool_bytes, dtype=torch.uint8,
                                                               device="cuda")
         self.pool_bytes = pool_bytes
         self.ctx = abi.sg_init(self.pool.data_ptr(), pool_bytes, policy, flags, max_tickets,
-                               n_streams, granule)
+                               n_streams, granule, n_gemm_streams)
         self._tables = None
 
     # -- life cycle
