@@ -5,9 +5,11 @@
     python -m paper_1712_04495_b300.kernel_cases triad [n, default 64M]      [launches]
     python -m paper_1712_04495_b300.kernel_cases fill  [rows, default 1e7]   [launches]
     python -m paper_1712_04495_b300.kernel_cases batch [jobs, default 10000] [launches]
+    python -m paper_1712_04495_b300.kernel_cases replay [jobs, default 10000] [launches] [policy]
 
 `batch` runs the tiny-job trace (10,000 jobs, 2 GiB pool) through the
-persistent grouped kernel on the device engine's replay plan.
+persistent grouped kernel on the device engine's replay plan. `replay` runs
+the device engine's replay (one warp, logical clock) of the same trace.
 
 The inputs are built by the library's own generators first (one launch per
 generator kernel), then the kernel runs `launches` times (default 3) on the
@@ -88,6 +90,19 @@ def run(kind: str, size: int | None = None, launches: int = 3, tile: str | None 
         info = abi.sg_batch_info(pl.batch)
         pl.close()
         return {"kernel": "batch", "jobs": len(tr), "ms": ms, "done": done, "err": err, **info}
+    if kind == "replay":
+        from . import runtime
+        tr = tg.trace_c4(n_jobs=size or 10_000)
+        pol = tile or "first_fit"
+        n = len(tr)
+        d_jobs = runtime.to_device(tr.jobs)
+        d_log = torch.empty(n * abi.RECORD_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        ws = torch.empty(abi.sg_replay_workspace_bytes(n), dtype=torch.uint8, device="cuda")
+        stats = torch.zeros(4, dtype=torch.int64, device="cuda")
+        ms = _time(lambda: abi.sg_replay(d_jobs.data_ptr(), n, tr.budget, 256, pol, 0, False, d_log.data_ptr(),
+                                         ws.data_ptr(), stats.data_ptr(), st), launches)
+        return {"kernel": "replay", "policy": pol, "jobs": n, "ms": ms, "us_per_event": 1e3 * ms / (2 * n),
+                "stats": stats.cpu().tolist()}
     raise ValueError(kind)
 
 
