@@ -133,7 +133,13 @@ class Server {
       return -e;
     }
     epfd_ = epoll_create1(EPOLL_CLOEXEC);
-    if (epfd_ < 0) return -errno;
+    if (epfd_ < 0) {
+      const int e = errno;
+      close(lfd_);
+      lfd_ = -1;
+      unlink(path_.c_str());
+      return -e;
+    }
     epoll_event ev{};
     ev.events = EPOLLIN;
     ev.data.fd = lfd_;
@@ -178,9 +184,10 @@ class Server {
       if (r == (ssize_t)sizeof m) return true;
       if (r < 0 && errno == EINTR) continue;
       if (r < 0 && (errno == EAGAIN || errno == EWOULDBLOCK)) {
-        // the client does not read: wait briefly, then drop the connection
+        // the client does not read: wait briefly, then give up on it (the
+        // caller drops the connection; other clients are not held up long)
         pollfd p{fd, POLLOUT, 0};
-        if (poll(&p, 1, 1000) == 1) continue;
+        if (poll(&p, 1, 100) == 1) continue;
       }
       return false;
     }
@@ -221,6 +228,11 @@ class Server {
     // cannot be reused by a new connection meanwhile
   }
 
+  // a reply that cannot be delivered drops the connection
+  void reply(int fd, const WireMsg& r) {
+    if (!send_msg(fd, r)) hang_up(fd);
+  }
+
   void on_message(int fd, Client& cl, const WireMsg& m) {
     WireMsg r{};
     r.ticket = m.ticket;
@@ -231,14 +243,14 @@ class Server {
       r.rc = eng_->pool_handle(r.payload, &r.c);
       r.prio = (int32_t)kWireVersion;
       cl.hello = true;
-      send_msg(fd, r);
+      reply(fd, r);
       return;
     }
     if (!cl.hello) {
       bump(&ServerCounters::protocol_errors);
       r.op = MSG_ERROR;
       r.rc = SG_ERR_INVALID;
-      send_msg(fd, r);
+      reply(fd, r);
       return;
     }
     if (m.op == MSG_DECLARE) {
@@ -256,7 +268,7 @@ class Server {
         cl.tickets.push_back(t);
         publish_open_counts();
       }
-      send_msg(fd, r);
+      reply(fd, r);
       return;
     }
     if (m.op == MSG_RELEASE) {
@@ -274,13 +286,13 @@ class Server {
           publish_open_counts();
         }
       }
-      send_msg(fd, r);
+      reply(fd, r);
       return;
     }
     bump(&ServerCounters::protocol_errors);
     r.op = MSG_ERROR;
     r.rc = SG_ERR_INVALID;
-    send_msg(fd, r);
+    reply(fd, r);
   }
 
   void accept_all() {
@@ -309,6 +321,7 @@ class Server {
       ssize_t r = recv(fd, &m, sizeof m, MSG_DONTWAIT);
       if (r == (ssize_t)sizeof m) {
         on_message(fd, it->second, m);
+        if (it->second.closed) return;
         continue;
       }
       if (r < 0 && (errno == EAGAIN || errno == EWOULDBLOCK)) return;
@@ -370,7 +383,7 @@ class Server {
           m.ticket = t;
           m.a = off;
           m.b = gt;
-          send_msg(fd, m);
+          reply(fd, m);
         }
         continue;
       }
@@ -380,7 +393,7 @@ class Server {
         m.op = MSG_TIMEOUT;
         m.ticket = t;
         m.rc = rc;
-        send_msg(fd, m);
+        reply(fd, m);
       }
       forget_ticket(t);
     }
