@@ -352,6 +352,7 @@ def batching_section(torch, abi, runtime, reps: int = 3) -> dict:
     out["persistent_kernel"] = {"jobs_per_s": n / (ms_b * 1e-3), "ms": ms_b, "chunks": binfo["chunks"],
                                 "blocks": binfo["blocks"], "launches": 1}
     out["plan_build_s"] = build_s
+    out["plan_build_parts_s"] = pl.build_s
     out["makespan_ratio_vs_serial"] = {"per_job_launch": statistics.median(t) / serial_s,
                                        "cuda_graph": ms_g * 1e-3 / serial_s,
                                        "persistent_kernel": ms_b * 1e-3 / serial_s}

@@ -64,10 +64,26 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
-// L2-coherent accesses for state shared by concurrently running kernels
-template <typename T>
-__device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
-template <typename T>
-__device__ __forceinline__ void stcg(T* p, T v) { __stcg(p, v); }
+// L2-coherent accesses (ld/st .cg) for state shared by concurrently running
+// kernels. The "memory" clobber keeps the compiler from moving them across
+// other memory operations and warp barriers: a lane must see what another
+// lane stored before a __syncwarp.
+#define SG_LDCG(T, PTX, C)                                                            \
+  __device__ __forceinline__ T ldcg(const T* p) {                                     \
+    T v;                                                                              \
+    asm volatile("ld.global.cg." PTX " %0, [%1];" : "=" C(v) : "l"(p) : "memory");   \
+    return v;                                                                         \
+  }                                                                                   \
+  __device__ __forceinline__ void stcg(T* p, T v) {                                   \
+    asm volatile("st.global.cg." PTX " [%0], %1;" ::"l"(p), C(v) : "memory");         \
+  }
+SG_LDCG(unsigned int, "u32", "r")
+SG_LDCG(int, "s32", "r")
+SG_LDCG(unsigned long, "u64", "l")
+SG_LDCG(long, "s64", "l")
+SG_LDCG(unsigned long long, "u64", "l")
+SG_LDCG(long long, "s64", "l")
+#undef SG_LDCG
+
 
 }  // namespace sg

@@ -139,17 +139,26 @@ class Planned:
     either as one CUDA graph or by the persistent grouped kernel."""
 
     def __init__(self, pool: torch.Tensor, jobs: np.ndarray, tables: torch.Tensor, policy="first_fit",
-                 keep: bool = False, budget: int | None = None):
+                 keep: bool = False, budget: int | None = None, graph: bool = True, batch: bool = True):
+        import time
         _require_cuda()
         self.pool = pool
         self.jobs = np.ascontiguousarray(jobs, dtype=tg.JOB_DTYPE)
         self.tables = tables
         self.budget = budget if budget is not None else pool.numel()
+        t0 = time.perf_counter()
         self.plan, self.plan_stats = replay(self.jobs, self.budget, policy)
+        t1 = time.perf_counter()
         self.keep = torch.zeros(len(jobs), dtype=torch.int64, device="cuda") if keep else None
         kp = self.keep.data_ptr() if keep else 0
-        self.graph = abi.sg_graph_build(pool.data_ptr(), self.budget, self.jobs, tables.data_ptr(), self.plan, kp)
-        self.batch = abi.sg_batch_build(pool.data_ptr(), self.budget, self.jobs, tables.data_ptr(), self.plan, kp)
+        self.graph = (abi.sg_graph_build(pool.data_ptr(), self.budget, self.jobs, tables.data_ptr(), self.plan, kp)
+                      if graph else 0)
+        t2 = time.perf_counter()
+        self.batch = (abi.sg_batch_build(pool.data_ptr(), self.budget, self.jobs, tables.data_ptr(), self.plan, kp)
+                      if batch else 0)
+        t3 = time.perf_counter()
+        # host seconds: the engine's plan (device replay incl. copies), graph and batch builds
+        self.build_s = {"replay": t1 - t0, "graph": t2 - t1, "batch": t3 - t2}
 
     def run_graph(self, stream: torch.cuda.Stream | None = None) -> int:
         if self.keep is not None:
