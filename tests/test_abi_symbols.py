@@ -54,3 +54,23 @@ def test_host_only_calls(lib):
     assert lib.sg_init(None, None, ctypes.c_uint64(0), None) == 4
     assert lib.sg_gemm_bf16(ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), 100, 128, 63,
                             None) == 4
+
+
+def test_gemm_tile_codes():
+    from paper_1712_04495_b300 import abi
+    assert abi.gemm_tile(256, 256) == (256 << 16) | 256
+    assert abi.gemm_tile_name(abi.gemm_tile(128, 64)) == "128x64"
+    assert abi.gemm_tile_name(128) == "128x128"          # a plain width names a 128-row tile
+    assert len(set(abi.GEMM_TILES)) == 4
+
+
+def test_config_struct_matches_the_header():
+    """sg_config's fields, in order, as the header declares them."""
+    import re
+    from paper_1712_04495_b300 import abi
+    text = open(os.path.join(ROOT, "include", "schedgpu.h")).read()
+    body = re.search(r"typedef struct sg_config \{(.*?)\} sg_config;", text, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = re.findall(r"\b(\w+);", body)
+    assert names == [n for n, _ in abi.SgConfig._fields_]
+    assert ctypes.sizeof(abi.SgConfig) == 32

@@ -216,6 +216,34 @@ def test_tickets_are_recycled_and_queue_positions_compacted(policy):
     s.shutdown()
 
 
+def test_cancel_and_grant_notifications():
+    """sg_cancel withdraws a waiting request (and reports a grant that came
+    first); sg_poll_grants lists grants in grant order, once each."""
+    abi, rt = _rt()
+    s = rt.Scheduler(MIB, "fifo")
+    cur = 0
+    a = s.declare(700 * 1024)
+    assert s.wait(a, 10 ** 9)[0] == abi.SG_OK
+    b = s.declare(700 * 1024)                      # waits
+    c = s.declare(100 * 1024)                      # waits behind b (strict FIFO)
+    torch.cuda.synchronize()
+    rc, cur, got = abi.sg_poll_grants(s.ctx, cur)
+    assert rc == abi.SG_OK and got == [a]
+    assert abi.sg_cancel(s.ctx, b)[0] == abi.SG_ERR_TIMEOUT   # withdrawn: c is now the head
+    rc, g = s.wait(c, 10 ** 9)
+    assert rc == abi.SG_OK
+    assert abi.sg_cancel(s.ctx, c)[0] == abi.SG_OK             # already granted
+    assert abi.sg_cancel(s.ctx, 999)[0] == abi.SG_ERR_INVALID  # never declared
+    rc, cur, got = abi.sg_poll_grants(s.ctx, cur)
+    assert rc == abi.SG_OK and got == [c]
+    rc, cur, got = abi.sg_poll_grants(s.ctx, cur)
+    assert got == []
+    s.release(a)
+    s.release(c)
+    torch.cuda.synchronize()
+    s.shutdown()
+
+
 def test_serving_results_equal_alone_and_in_the_mix():
     # open-loop arrivals admitted while earlier requests run; every request's
     # output equals its output when it runs alone on the GPU
