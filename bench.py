@@ -437,6 +437,95 @@ def _latency_client(path: str, reps: int, q) -> None:
     q.put({"connect_us": 1e6 * t_conn, "pre_allocation_us": med(t_decl), "post_free_us": med(t_rel)})
 
 
+def _serving_client(path: str, jobs: list, go, q) -> None:
+    """Client process of `processes_section`: triad jobs (n, key) one after
+    another on its own stream, each declared, run on the IPC-mapped grant,
+    synchronised and released."""
+    sys.path.insert(0, ROOT)
+    import torch
+    from paper_1712_04495_b300 import abi as a
+    torch.cuda.set_device(0)
+    torch.zeros(1, device="cuda")
+    cl = a.sg_client_connect(path)
+    a.sg_client_pool(cl)
+    st = torch.cuda.Stream()
+    q.put(("ready", 0.0, []))
+    go.wait()
+    t_start = time.perf_counter()
+    turn = []
+    for n, key in jobs:
+        t0 = time.perf_counter()
+        tk = a.sg_client_declare(cl, 12 * n)
+        rc, g = a.sg_client_wait(cl, tk, 60 * 10 ** 9)
+        if rc != a.SG_OK:
+            q.put(("error", 0.0, [rc]))
+            return
+        b, c = g.ptr + 4 * n, g.ptr + 8 * n
+        a.sg_gen_triad(b, c, n, key, st.cuda_stream)
+        a.sg_triad(g.ptr, b, c, 3.0, n, st.cuda_stream)
+        st.synchronize()
+        a.sg_client_release(cl, tk)
+        turn.append(time.perf_counter() - t0)
+    q.put(("done", time.perf_counter() - t_start, turn))
+    a.sg_client_close(cl)
+
+
+def processes_section(torch, abi, runtime, clients: int = 4, jobs_per_client: int = 50) -> dict:
+    """The paper's setting: separate client processes sharing one GPU through
+    the scheduler (server process, UNIX socket, CUDA IPC). Triad jobs with n
+    log-uniform in [1M, 64M], all ready at once. The same jobs run in one
+    process through the trace runner, co-scheduled and exclusive-serial."""
+    import multiprocessing as mp
+    import tempfile
+    n_jobs = clients * jobs_per_client
+    tr = tg.trace_single_kind_t0(7, n_jobs, 1 << 20, 1 << 26, 16 << 30, f"triad{n_jobs}_t0_16GiB")
+    pool = torch.empty(tr.budget, dtype=torch.uint8, device="cuda")
+    sched = runtime.Scheduler(tr.budget, "first_fit", pool=pool)
+    path = os.path.join(tempfile.mkdtemp(prefix="sg_bench_"), "sock")
+    srv = abi.sg_server_start(sched.ctx, path)
+    ctx = mp.get_context("spawn")
+    q, go = ctx.Queue(), ctx.Event()
+    work = [[] for _ in range(clients)]
+    for j in range(n_jobs):
+        work[j % clients].append((int(tr.jobs["p0"][j]), int(tr.jobs["key"][j])))
+    procs = [ctx.Process(target=_serving_client, args=(path, work[i], go, q)) for i in range(clients)]
+    for p in procs:
+        p.start()
+    out = {"workload": tr.name, "clients": clients, "jobs": n_jobs}
+    try:
+        for _ in range(clients):
+            assert q.get(timeout=300)[0] == "ready"
+        t0 = time.perf_counter()
+        go.set()
+        turns = []
+        for _ in range(clients):
+            kind, _, turn = q.get(timeout=600)
+            assert kind == "done", (kind, turn)
+            turns += turn
+        wall = time.perf_counter() - t0
+    finally:
+        for p in procs:
+            p.join(60)
+        abi.sg_server_stop(srv)
+        sched.shutdown()
+    turns = np.sort(np.array(turns))
+    out["processes"] = {"jobs_per_s": n_jobs / wall, "ms": 1e3 * wall,
+                        "turnaround_p50_ms": 1e3 * float(turns[len(turns) // 2]),
+                        "turnaround_p99_ms": 1e3 * float(turns[min(len(turns) - 1, int(0.99 * len(turns)))])}
+    s = runtime.Scheduler(tr.budget, "first_fit", pool=pool)
+    d_jobs, d_tab = runtime.to_device(tr.jobs), runtime.device_tables(tr)
+    for name, mode in (("one_process", abi.SG_RUN_SATURATED),
+                       ("one_process_exclusive", abi.SG_RUN_SATURATED | abi.SG_RUN_EXCLUSIVE)):
+        s.run_trace(d_jobs, d_tab, mode)
+        rc, _, _, st = s.run_trace(d_jobs, d_tab, mode)
+        assert rc == abi.SG_OK
+        out[name] = {"jobs_per_s": n_jobs / (st["makespan_ns"] * 1e-9), "ms": st["makespan_ns"] / 1e6}
+    s.shutdown()
+    del pool
+    torch.cuda.empty_cache()
+    return out
+
+
 def client_server_section(torch, abi, runtime, reps: int = 300) -> dict:
     """The same life-cycle stages from a separate client process through the
     scheduler server (UNIX socket; grants pushed by the server): the paper's
@@ -682,6 +771,7 @@ def main():
         if not args.no_extras:
             extra["lifecycle"] = lifecycle_section(torch, abi, runtime)
             extra["client_server"] = client_server_section(torch, abi, runtime)
+            extra["processes"] = processes_section(torch, abi, runtime)
             extra["policies"] = policies_section(torch, abi, runtime)
             extra["engine"] = engine_section(torch, abi, runtime)
             extra["kinds"] = kinds_section(torch, abi, runtime)
