@@ -354,6 +354,16 @@ int sg_batch_destroy(sg_batch* b);
 
 /* Engine error flags of the context (0 = none). */
 uint32_t sg_device_error(sg_ctx* ctx);
+
+/* Post-mortem view of the device engine's scalar state (the shared data of
+ * Sec. III-B). Taken after ctx's control stream and stream slots have
+ * finished their work; jobs launched by the caller on other streams may
+ * still change it. */
+typedef struct sg_state_summary {
+    uint64_t budget, used, peak_used, max_free_extent, grants, passes, frag_waits;
+    uint32_t policy, free_extents, waiting, done, error_flags, reserved;
+} sg_state_summary;
+int sg_state(sg_ctx* ctx, sg_state_summary* out);
 const char* sg_strerror(int code);
 
 /* ------------------------------------------------------ job kernels */

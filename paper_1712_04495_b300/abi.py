@@ -55,6 +55,17 @@ class SgRunStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class SgStateSummary(ctypes.Structure):
+    _fields_ = [("budget", ctypes.c_uint64), ("used", ctypes.c_uint64), ("peak_used", ctypes.c_uint64),
+                ("max_free_extent", ctypes.c_uint64), ("grants", ctypes.c_uint64), ("passes", ctypes.c_uint64),
+                ("frag_waits", ctypes.c_uint64), ("policy", ctypes.c_uint32), ("free_extents", ctypes.c_uint32),
+                ("waiting", ctypes.c_uint32), ("done", ctypes.c_uint32), ("error_flags", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 class SgServerCounts(ctypes.Structure):
     _fields_ = [("clients_accepted", ctypes.c_uint64), ("clients_reaped", ctypes.c_uint64),
                 ("declares", ctypes.c_uint64), ("grants", ctypes.c_uint64), ("timeouts", ctypes.c_uint64),
@@ -128,6 +139,7 @@ _SIGS = {
     "sg_client_wait": ([_P, _U32, _U64, _P], ctypes.c_int),
     "sg_client_release": ([_P, _U32, _U64], ctypes.c_int),
     "sg_client_close": ([_P], ctypes.c_int),
+    "sg_state": ([_P, _P], ctypes.c_int),
 }
 
 _lib = None
@@ -202,6 +214,13 @@ def sg_wait(ctx: int, ticket: int, timeout_ns: int):
 
 def sg_release(ctx: int, ticket: int, nbytes: int = 0, stream: int = 0) -> int:
     return lib().sg_release(ctx, ticket, nbytes, stream)
+
+
+def sg_state(ctx: int) -> dict:
+    """Post-mortem summary of the device engine's scalar state."""
+    st = SgStateSummary()
+    _check(lib().sg_state(ctx, ctypes.byref(st)), "sg_state")
+    return st.as_dict()
 
 
 def sg_cancel(ctx: int, ticket: int):

@@ -15,6 +15,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "engine.cuh"
 #include "jobs.h"
 
@@ -407,6 +409,29 @@ extern "C" int sg_reset(sg_ctx* c) {
 
 extern "C" uint32_t sg_device_error(sg_ctx* c) { return c ? c->h_hdr[1] : 0u; }
 
+extern "C" int sg_state(sg_ctx* c, sg_state_summary* out) {
+  if (!c || !out) return SG_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  for (auto s : c->slots) CK(cudaStreamSynchronize(s));
+  CK(cudaStreamSynchronize(c->ctrl));
+  EngHdr h;
+  CK(cudaMemcpy(&h, c->eng.hdr, sizeof h, cudaMemcpyDeviceToHost));
+  memset(out, 0, sizeof *out);
+  out->budget = h.budget;
+  out->used = h.used;
+  out->peak_used = h.peak_used;
+  out->max_free_extent = h.max_ext;
+  out->grants = h.seq;
+  out->passes = h.passes;
+  out->frag_waits = h.frag_waits;
+  out->policy = h.policy;
+  out->free_extents = h.n_ext;
+  out->waiting = h.q_len;
+  out->done = h.n_done;
+  out->error_flags = h.err;
+  return SG_OK;
+}
+
 // Tickets whose life is over: the full release has run on the device (it
 // was requested by sg_release or is done by the job itself), or the request
 // timed out. The device keeps no reference to them; they may be reused.
@@ -573,6 +598,11 @@ extern "C" int sg_run_trace(sg_ctx* c, const sg_job* jobs, uint32_t n, const uin
   const bool want_keep = (mode & SG_RUN_KEEP) && keep;
   int rc = ctx_reset_locked(c);
   if (rc != SG_OK) return rc;
+  // profiler range over the whole trace (no cost without a profiler)
+  struct Range {
+    Range() { nvtxRangePushA("sg_run_trace"); }
+    ~Range() { nvtxRangePop(); }
+  } range;
   std::vector<sg_job> hj(n);
   if (n) {
     if (host_io) {

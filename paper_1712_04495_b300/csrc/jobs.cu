@@ -2,6 +2,7 @@
 // generators of all three job kinds, and the output digest. Each kernel
 // that ends a job carries a RelHook: its last block releases the job's
 // ticket on the device engine (post-free of Sec. IV).
+#include <nvtx3/nvToolsExt.h>
 #include "engine.cuh"
 #include "jobs.h"
 #include "tiles.cuh"
@@ -195,6 +196,11 @@ GemmLayout gemm_layout(uint64_t m, uint64_t n, uint64_t k) {
 // Generator + kernel (+ digest) of one job in its grant, on one stream.
 int launch_job(const sg_job& job, char* base, const uint64_t* tables, const RelHook& hook,
                uint64_t* keep_slot, uint32_t* err, cudaStream_t st, uint64_t* launches) {
+  static const char* kRange[3] = {"job triad", "job spmv", "job gemm"};
+  nvtxRangePushA(job.kind <= SG_KIND_GEMM ? kRange[job.kind] : "job");   // host side of the launch
+  struct Pop {
+    ~Pop() { nvtxRangePop(); }
+  } pop;
   RelHook none = hook;
   none.active = 0;
   const RelHook& last = keep_slot ? none : hook;

@@ -128,6 +128,11 @@ def test_trace_alone_equals_mix(policy):
     assert np.all(rec2["grant_t"][order][1:] >= rec2["done_t"][order][:-1])
     # each job's result is the same alone and in the mix
     assert torch.equal(keep, keep2)
+    # every grant came back: one free extent spanning the pool, nobody waiting
+    eng = abi.sg_state(s.ctx)
+    assert eng["used"] == 0 and eng["waiting"] == 0 and eng["error_flags"] == 0
+    assert eng["free_extents"] == 1 and eng["max_free_extent"] == eng["budget"] == budget
+    assert eng["done"] == len(tr) and eng["grants"] == len(tr)
     for j in np.nonzero(tr.jobs["kind"] == tg.KIND_TRIAD)[0]:
         ref = K.triad(int(tr.jobs["key"][j]), int(tr.jobs["p0"][j]))
         assert int(keep[j].item()) & ((1 << 64) - 1) == _digest_f32(ref)
