@@ -264,7 +264,7 @@ def kernel_roofline(torch, abi, peaks):
     ms = e0.elapsed_time(e1) / reps
     gbs = 12.0 * n / (ms * 1e-3) / 1e9
     out["triad"] = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": gbs / peaks["hbm_gbs"], "traffic": None, "ms": ms,
+                    "frac": gbs / peaks["hbm_gbs"], "traffic": profiled_traffic("triad_fp32_64M"), "ms": ms,
                     "kernel": "k_triad n=64M", "bytes_per_launch": 12 * n}
     del buf
     # FP32 CSR SpMV, 1e7 rows, Poisson(16) non-zeros per row
@@ -291,7 +291,8 @@ def kernel_roofline(torch, abi, peaks):
     alg = 4 * (rows + 1) + 8 * nnz + 8 * rows
     gbs = alg / (ms * 1e-3) / 1e9
     out["spmv"] = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                   "frac": gbs / peaks["hbm_gbs"], "traffic": None, "ms": ms,
+                   "frac": gbs / peaks["hbm_gbs"], "traffic": profiled_traffic("spmv_csr_1e7rows_poisson16"),
+                   "ms": ms,
                    "kernel": "k_spmv<int> rows=1e7 nnz/row~Poisson(16)", "bytes_per_launch": alg}
     del base
     torch.cuda.synchronize()
