@@ -354,6 +354,15 @@ def batching_section(torch, abi, runtime, reps: int = 3) -> dict:
                                 "blocks": binfo["blocks"], "launches": 1}
     out["plan_build_s"] = build_s
     out["plan_build_parts_s"] = pl.build_s
+    # admission inside the persistent kernel: no plan, the batch's engine
+    # releases and grants as jobs finish
+    for pol in ("first_fit", "fifo"):
+        ob = runtime.OnlineBatch(pool, tr.jobs, tab, pol, budget=tr.budget)
+        ms_o = timed(lambda: ob.run())
+        rc, done, err = ob.status()
+        assert rc == abi.SG_OK and done == n, (rc, done, err)
+        ob.close()
+        out[f"persistent_online_{pol}"] = {"jobs_per_s": n / (ms_o * 1e-3), "ms": ms_o, "plan": "none"}
     out["makespan_ratio_vs_serial"] = {"per_job_launch": statistics.median(t) / serial_s,
                                        "cuda_graph": ms_g * 1e-3 / serial_s,
                                        "persistent_kernel": ms_b * 1e-3 / serial_s}

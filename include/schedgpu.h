@@ -348,6 +348,23 @@ int sg_batch_build(void* dev_pool, uint64_t pool_bytes, const sg_job* jobs, uint
                    sg_batch** out);
 int sg_batch_launch(sg_batch* b, void* stream);
 int sg_batch_status(sg_batch* b, uint64_t* jobs_done, uint32_t* err_flags);
+
+/* A batch that admits on the device instead of from a plan: the batch owns
+ * an engine (policy SG_POLICY_*, the pool as budget, granule 256) that holds
+ * every job declared at t = 0. The persistent kernel's first policy pass
+ * grants what fits. The worker that finishes a job releases its memory under
+ * the engine lock, and the jobs that the release's notification pass grants
+ * are enqueued at once. Nothing is planned in advance and the host is not
+ * involved. Jobs as for sg_batch_build (host array);
+ * SG_ERR_TOO_LARGE if a job could never fit the pool. Run it with
+ * sg_batch_launch; sg_batch_status, sg_batch_info and sg_batch_destroy apply
+ * as for a planned batch. */
+int sg_batch_build_online(void* dev_pool, uint64_t pool_bytes, const sg_job* jobs, uint32_t n,
+                          const uint64_t* tables_dev, uint32_t policy, uint64_t* keep_dev, sg_batch** out);
+/* The admission log of the last launch of an online batch (n records, host
+ * memory): grant order, grant and completion times (%globaltimer), offsets.
+ * SG_ERR_INVALID for a planned batch. Synchronous. */
+int sg_batch_records(sg_batch* b, sg_record* out);
 /* jobs planned, chunks in the batch, workers (four per SM) of the launch */
 int sg_batch_info(const sg_batch* b, uint64_t* jobs, uint64_t* chunks, uint64_t* workers);
 int sg_batch_destroy(sg_batch* b);

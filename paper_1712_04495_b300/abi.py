@@ -140,6 +140,8 @@ _SIGS = {
     "sg_client_release": ([_P, _U32, _U64], ctypes.c_int),
     "sg_client_close": ([_P], ctypes.c_int),
     "sg_state": ([_P, _P], ctypes.c_int),
+    "sg_batch_build_online": ([_P, _U64, _P, _U32, _P, _U32, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "sg_batch_records": ([_P, _P], ctypes.c_int),
 }
 
 _lib = None
@@ -366,6 +368,22 @@ def sg_batch_build(pool_ptr: int, pool_bytes: int, jobs: np.ndarray, tables_ptr:
     _check(lib().sg_batch_build(pool_ptr, pool_bytes, jobs.ctypes.data, len(jobs), tables_ptr or None,
                                 plan.ctypes.data, keep_ptr or None, ctypes.byref(out)), "sg_batch_build")
     return out.value
+
+
+def sg_batch_build_online(pool_ptr: int, pool_bytes: int, jobs: np.ndarray, tables_ptr: int, policy,
+                          keep_ptr: int = 0) -> int:
+    jobs = np.ascontiguousarray(jobs, dtype=JOB_DTYPE)
+    pol = POLICIES[policy] if isinstance(policy, str) else int(policy)
+    out = _P()
+    _check(lib().sg_batch_build_online(pool_ptr, pool_bytes, jobs.ctypes.data, len(jobs), tables_ptr or None, pol,
+                                       keep_ptr or None, ctypes.byref(out)), "sg_batch_build_online")
+    return out.value
+
+
+def sg_batch_records(b: int, n: int) -> np.ndarray:
+    out = np.zeros(n, dtype=RECORD_DTYPE)
+    _check(lib().sg_batch_records(b, out.ctypes.data), "sg_batch_records")
+    return out
 
 
 def sg_batch_launch(b: int, stream: int = 0) -> int:

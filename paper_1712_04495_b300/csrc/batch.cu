@@ -14,6 +14,15 @@
 // share memory never overlap in time. There is no host round trip and no
 // launch per job.
 //
+// Admitting on the device instead (sg_batch_build_online): there is no plan.
+// The batch's own engine holds every job declared at t = 0. One warp of the
+// kernel (in a block of its own) owns that engine for the whole launch, so it
+// reads the state through L1, as a replay does: it runs the first policy pass, then takes finished
+// jobs from a completion ring in the order the workers finish them, releases
+// each (post-free and its notification pass) and enqueues the first phase of
+// every job the pass grants, at the offset the engine gave it. Admission and
+// execution share the kernel.
+//
 // The work queue is a ring of exactly `total` slots (the chunk count of the
 // whole batch, known in advance): slot i is written once, and its sequence
 // word becomes i + 1 when the item is visible. A block claims the next slot
@@ -50,7 +59,7 @@ struct Item {
 
 struct BatchDev {
   const sg_job* jobs;
-  const uint64_t* offset;        // [n] grant offsets (the plan)
+  uint64_t* offset;              // [n] grant offsets (the plan, or written at grant time)
   char* pool;
   const uint64_t* tables;
   uint64_t* keep;                // [n] output digests, or null
@@ -63,6 +72,12 @@ struct BatchDev {
   unsigned long long* ctr;       // [0] head (claims), [1] tail (reservations), [2] jobs done
   uint32_t* err;
   uint64_t total;
+  Eng eng;                       // the batch's engine when it admits on the device
+  uint32_t online;
+  uint32_t n;
+  uint32_t* comp;                // [n] finished jobs, in finishing order (online)
+  uint32_t* comp_seq;            // [n] slot r holds r + 1 once comp[r] is visible
+  uint32_t* glist;               // [n] granted jobs, in grant order (online)
 };
 
 __host__ __device__ inline uint32_t gemm_bn_small(uint64_t n) { return n > 64 ? 128u : 64u; }
@@ -117,6 +132,127 @@ __device__ void push_phase(const BatchDev& B, uint32_t job, uint32_t ph) {
   }
   __threadfence();
   for (uint64_t i = 0; i < cnt; i++) atomicExch(B.seq + base + i, (uint32_t)(base + i + 1));
+}
+
+// The same, warp-wide (one full warp): the chunks of the phase are written
+// and published by all 32 lanes.
+__device__ void push_phase_warp(const BatchDev& B, uint32_t job, uint32_t ph) {
+  const uint64_t cnt = phase_chunks(B.jobs[job], ph);
+  unsigned long long base = 0;
+  if (lane_id() == 0) {
+    stcg(B.left + job, (uint32_t)cnt);
+    __threadfence();
+    base = atomicAdd(&B.ctr[1], (unsigned long long)cnt);
+    if (base + cnt > B.total) atomicOr(B.err, ERR_CAP);
+  }
+  base = __shfl_sync(SG_FULL, base, 0);
+  if (base + cnt > B.total) return;           // warp-uniform
+  for (uint64_t i = lane_id(); i < cnt; i += 32) {
+    Item it;
+    it.job = job;
+    it.phase = ph;
+    it.chunk = i;
+    B.items[base + i] = it;
+  }
+  __threadfence();                            // each lane's items before its sequence words
+  for (uint64_t i = lane_id(); i < cnt; i += 32) stcg(B.seq + base + i, (uint32_t)(base + i + 1));
+  __syncwarp();
+}
+
+// Online admission. The engine warp hands every job it grants to the
+// block's other 31 warps: it appends the job to the batch's grant list (n
+// entries, so nothing wraps) and bumps a shared-memory tail; they enqueue the
+// jobs' first phases, so the engine's serial path only runs engine steps.
+struct GrantQueue {                 // shared memory of the engine's block
+  uint32_t tail, claim, done;
+};
+
+// bounded spin of one lane on a shared word until pred() holds; false = gave up
+template <class Pred>
+__device__ bool spin_until(const BatchDev& B, Pred pred) {
+  uint64_t t0 = 0;
+  unsigned ns = 32;
+  for (uint32_t it = 0;; it++) {
+    if (pred()) return true;
+    if ((it & 15) == 15) {
+      if (ldcg(B.err) != 0) return false;
+      const uint64_t now = globaltimer_ns();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > kBatchWaitNs) { atomicOr(B.err, ERR_LOCK); return false; }
+    }
+    __nanosleep(ns);
+    if (ns < 256) ns <<= 1;
+  }
+}
+
+// the engine warp: give the jobs granted at ring positions [from, to) their
+// offsets and queue them for the publishers (lane 0)
+__device__ bool hand_over(const BatchDev& B, const Eng& E, GrantQueue* Q, uint32_t from, uint32_t to) {
+  bool ok = true;
+  if (lane_id() == 0) {
+    for (uint32_t p = from; p < to && ok; p++) {
+      const uint32_t j = eld(E, E.dev_ring + p % B.n);
+      stcg(B.offset + j, eld(E, reinterpret_cast<const uint64_t*>(E.rec + j) + 3));   // sg_record.offset
+      volatile GrantQueue* vq = Q;
+      const uint32_t t = vq->tail;
+      if (t >= B.n) { atomicOr(B.err, ERR_CAP); ok = false; break; }   // cannot happen: n grants
+      stcg(B.glist + t, j);
+      __threadfence();                        // offset and list entry before the tail moves
+      vq->tail = t + 1;
+    }
+  }
+  return __shfl_sync(SG_FULL, (int)ok, 0) != 0;
+}
+
+// The engine warp of an online batch (the only user of the batch's engine
+// state during the launch).
+__device__ void engine_service(const BatchDev& B, GrantQueue* Q) {
+  const Eng E = eng_owned(B.eng);
+  Sess s = sess_load(E);
+  uint32_t from = s.ring_tail;
+  policy_pass(E, s, globaltimer_ns(), nullptr, nullptr);
+  bool ok = hand_over(B, E, Q, from, s.ring_tail);
+  for (uint32_t r = 0; r < B.n && s.err == 0 && ok; r++) {
+    uint32_t j = 0;
+    if (lane_id() == 0) {                     // the r-th finished job
+      ok = spin_until(B, [&] { return ldcg(B.comp_seq + r) == r + 1; });
+      __threadfence();
+      if (ok) j = ldcg(B.comp + r);
+    }
+    ok = __shfl_sync(SG_FULL, (int)ok, 0) != 0;
+    j = __shfl_sync(SG_FULL, j, 0);
+    if (!ok) break;
+    from = s.ring_tail;
+    op_release(E, s, j, 0, globaltimer_ns(), nullptr, nullptr);
+    ok = hand_over(B, E, Q, from, s.ring_tail);
+  }
+  if (s.err && lane_id() == 0) atomicOr(B.err, s.err);
+  sess_store(E, s);
+  if (lane_id() == 0) {
+    __threadfence_block();
+    ((volatile GrantQueue*)Q)->done = 1;
+  }
+  __syncwarp();
+}
+
+// a publisher warp of the engine's block: enqueue the first phase of each
+// queued grant until the engine warp is done
+__device__ void publish_service(const BatchDev& B, GrantQueue* Q) {
+  volatile GrantQueue* vq = Q;
+  for (;;) {
+    uint32_t c = 0;
+    int have = 0;
+    if (lane_id() == 0) {
+      c = atomicAdd(&Q->claim, 1u);
+      bool ok = spin_until(B, [&] { return c < vq->tail || vq->done; });
+      have = ok && c < vq->tail;
+    }
+    have = __shfl_sync(SG_FULL, have, 0);
+    c = __shfl_sync(SG_FULL, c, 0);
+    if (!have) break;
+    __threadfence();
+    push_phase_warp(B, ldcg(B.glist + c), 0);
+  }
 }
 
 // Claim the next slot; 1 = item in *out, 0 = nothing left, -1 = gave up.
@@ -236,6 +372,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchDev B) {
   __shared__ uint32_t tmem_base;
   __shared__ __align__(8) uint64_t mbar[kGroups];
   __shared__ volatile uint32_t s_abort;
+  __shared__ GrantQueue gq;
 
   const uint32_t gi = threadIdx.x / kChunkThreads;
   const SubGroup g{gi * kChunkThreads, 1u + gi};
@@ -256,14 +393,24 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchDev B) {
   tc_fence_after();
   const uint32_t tmem = tmem_base + gi * (kBatchTmemCols / kGroups);
   uint32_t mphase = 0;
+  // admitting on the device: block 0 serves the engine (warp 0) and
+  // publishes what it grants (the other warps); no chunk work shares the L1
+  // that holds the engine state
+  const bool service = B.online && blockIdx.x == 0;
+  if (service) {
+    if (threadIdx.x == 0) gq.tail = gq.claim = gq.done = 0;
+    __syncthreads();
+    if (threadIdx.x < 32) engine_service(B, &gq);
+    else publish_service(B, &gq);
+  }
 
-  for (;;) {
+  for (; !service;) {
     if (g.t() == 0) action[gi] = pop(B, &cur[gi]);
     g.sync();
     if (action[gi] != 1) break;
     const Item it = cur[gi];
     const sg_job& job = B.jobs[it.job];
-    char* base = B.pool + B.offset[it.job];
+    char* base = B.pool + ldcg(B.offset + it.job);
     const bool keep = B.keep != nullptr;
     const uint32_t nph = job_phases(job, keep);
     const bool digest = keep && it.phase == nph - 1;
@@ -347,7 +494,15 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchDev B) {
     if (s_last[gi]) {
       __threadfence();
       if (it.phase + 1 < nph) {
-        if (g.t() == 0) push_phase(B, it.job, it.phase + 1);
+        if (g.t() < 32) push_phase_warp(B, it.job, it.phase + 1);
+      } else if (B.online) {
+        if (g.t() == 0) {                             // hand the job to the engine warp
+          const uint64_t r = atomicAdd(&B.ctr[3], 1ull);
+          stcg(B.comp + r, it.job);
+          __threadfence();
+          atomicExch(B.comp_seq + r, (uint32_t)(r + 1));
+          atomicAdd(&B.ctr[2], 1ull);
+        }
       } else {
         for (uint64_t e = B.succ_ptr[it.job] + g.t(); e < B.succ_ptr[it.job + 1]; e += kChunkThreads) {
           const uint32_t s2 = B.succ[e];
@@ -372,11 +527,44 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchDev B) {
 
 using namespace sg;
 
+namespace {
+
+bool batch_kernel_attributes() {
+  bool ok = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) ==
+            cudaSuccess;
+  // the largest shared-memory split for the kernel's staging buffers
+  ok &= cudaFuncSetAttribute(k_batch, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess;
+  return ok;
+}
+
+// one block (four workers) per SM: a kernel that allocates TMEM gets one
+int batch_grid(uint64_t total) {
+  int grid = num_sms();
+  if ((uint64_t)grid * kGroups > total && total > 0) grid = (int)((total + kGroups - 1) / kGroups);
+  return grid;
+}
+
+// the job checks both builds make
+int batch_job_ok(const sg_job& jb, const uint64_t* tables_dev) {
+  if (jb.kind > SG_KIND_GEMM) return SG_ERR_INVALID;
+  if (jb.kind == SG_KIND_GEMM && (jb.p2 == 0 || jb.p2 % 8 || jb.p0 == 0 || jb.p1 == 0)) return SG_ERR_INVALID;
+  if (jb.kind == SG_KIND_SPMV && (!tables_dev || jb.p0 == 0)) return SG_ERR_INVALID;
+  if (jb.kind == SG_KIND_TRIAD && jb.p0 == 0) return SG_ERR_INVALID;
+  return SG_OK;
+}
+
+}  // namespace
+
 struct sg_batch {
   char* dev = nullptr;           // one allocation: every device array below
   BatchDev d{};
   uint32_t n = 0, granted = 0;
   int grid = 0;
+  // admitting on the device
+  bool online = false;
+  uint64_t budget = 0, granule = 256;
+  uint32_t policy = 0;
   // launch-time initial state, kept on the device
   uint32_t* dep0 = nullptr;
   uint32_t* left0 = nullptr;
@@ -396,10 +584,7 @@ extern "C" int sg_batch_build(void* dev_pool, uint64_t pool_bytes, const sg_job*
   uint64_t total = 0;
   for (uint32_t j : pd.order) {
     const sg_job& jb = jobs[j];
-    if (jb.kind > SG_KIND_GEMM) return SG_ERR_INVALID;
-    if (jb.kind == SG_KIND_GEMM && (jb.p2 == 0 || jb.p2 % 8 || jb.p0 == 0 || jb.p1 == 0)) return SG_ERR_INVALID;
-    if (jb.kind == SG_KIND_SPMV && (!tables_dev || jb.p0 == 0)) return SG_ERR_INVALID;
-    if (jb.kind == SG_KIND_TRIAD && jb.p0 == 0) return SG_ERR_INVALID;
+    if (batch_job_ok(jb, tables_dev) != SG_OK) return SG_ERR_INVALID;
     granted[j] = 1;
     for (uint32_t ph = 0; ph < job_phases(jb, keep); ph++) total += phase_chunks(jb, ph);
   }
@@ -449,26 +634,18 @@ extern "C" int sg_batch_build(void* dev_pool, uint64_t pool_bytes, const sg_job*
   if (!items0.empty())
     okc &= cudaMemcpy(d + o_items0, items0.data(), sizeof(Item) * items0.size(), cudaMemcpyHostToDevice) ==
            cudaSuccess;
-  int per_sm = 0;
-  okc &= cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) == cudaSuccess;
-  // the largest shared-memory split, so four blocks (and their TMEM) fit an SM
-  okc &= cudaFuncSetAttribute(k_batch, cudaFuncAttributePreferredSharedMemoryCarveout,
-                              (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess;
-  okc &= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kBatchThreads, kBatchSmem) == cudaSuccess;
+  okc &= batch_kernel_attributes();
   if (!okc) {
     cudaFree(b->dev);
     delete b;
     return SG_ERR_CUDA;
   }
-  // one block (four workers) per SM: a kernel that allocates TMEM gets one
-  per_sm = 1;
   b->n = n;
   b->granted = (uint32_t)pd.order.size();
-  b->grid = per_sm * num_sms();
-  if ((uint64_t)b->grid * kGroups > total && total > 0) b->grid = (int)((total + kGroups - 1) / kGroups);
+  b->grid = batch_grid(total);
   BatchDev& B = b->d;
   B.jobs = (const sg_job*)(d + o_jobs);
-  B.offset = (const uint64_t*)(d + o_off);
+  B.offset = (uint64_t*)(d + o_off);
   B.pool = (char*)dev_pool;
   B.tables = tables_dev;
   B.keep = keep_dev;
@@ -489,6 +666,81 @@ extern "C" int sg_batch_build(void* dev_pool, uint64_t pool_bytes, const sg_job*
   return SG_OK;
 }
 
+extern "C" int sg_batch_build_online(void* dev_pool, uint64_t pool_bytes, const sg_job* jobs, uint32_t n,
+                                     const uint64_t* tables_dev, uint32_t policy, uint64_t* keep_dev,
+                                     sg_batch** out) {
+  if (!out || !dev_pool || (!jobs && n) || policy > SG_POLICY_PRIO_FIRST_FIT) return SG_ERR_INVALID;
+  *out = nullptr;
+  const uint64_t granule = 256;
+  const uint64_t budget = pool_bytes / granule * granule;
+  if (budget / granule > kKeyNeedMask) return SG_ERR_INVALID;
+  const bool keep = keep_dev != nullptr;
+  uint64_t total = 0;
+  for (uint32_t j = 0; j < n; j++) {
+    const sg_job& jb = jobs[j];
+    if (batch_job_ok(jb, tables_dev) != SG_OK) return SG_ERR_INVALID;
+    if ((jb.need + granule - 1) / granule * granule > budget) return SG_ERR_TOO_LARGE;   // would never run
+    if (jb.prio < -32768 || jb.prio > 32767) return SG_ERR_INVALID;
+    for (uint32_t ph = 0; ph < job_phases(jb, keep); ph++) total += phase_chunks(jb, ph);
+  }
+  if (total > 0xFFFFFFF0ull) return SG_ERR_CAPACITY;
+  auto a256 = [](uint64_t x) { return (x + 255) / 256 * 256; };
+  const uint64_t nn = n ? n : 1, tt = total ? total : 1;
+  uint64_t o = 0;
+  const uint64_t o_jobs = o; o += a256(sizeof(sg_job) * nn);
+  const uint64_t o_off = o; o += a256(8 * nn);
+  const uint64_t o_left = o; o += a256(4 * nn);
+  const uint64_t o_items = o; o += a256(sizeof(Item) * tt);
+  const uint64_t o_seq = o; o += a256(4 * tt);
+  const uint64_t o_ctr = o; o += 256;
+  const uint64_t o_err = o; o += 256;
+  const uint64_t o_comp = o; o += a256(4 * nn);
+  const uint64_t o_cseq = o; o += a256(4 * nn);
+  const uint64_t o_glist = o; o += a256(4 * nn);
+  const uint64_t o_eng = o; o += a256(batch_engine_bytes((uint32_t)nn));
+  sg_batch* b = new sg_batch();
+  if (cudaMalloc(&b->dev, o) != cudaSuccess) {
+    delete b;
+    return SG_ERR_CUDA;
+  }
+  char* d = b->dev;
+  bool okc = n == 0 || cudaMemcpy(d + o_jobs, jobs, sizeof(sg_job) * n, cudaMemcpyHostToDevice) == cudaSuccess;
+  okc &= batch_kernel_attributes();
+  if (!okc) {
+    cudaFree(b->dev);
+    delete b;
+    return SG_ERR_CUDA;
+  }
+  b->n = n;
+  b->granted = n;
+  b->grid = batch_grid(total) + 1;                   // block 0 serves the engine
+  if (b->grid > num_sms()) b->grid = num_sms();
+  b->online = true;
+  b->budget = budget;
+  b->granule = granule;
+  b->policy = policy;
+  BatchDev& B = b->d;
+  B.jobs = (const sg_job*)(d + o_jobs);
+  B.offset = (uint64_t*)(d + o_off);
+  B.pool = (char*)dev_pool;
+  B.tables = tables_dev;
+  B.keep = keep_dev;
+  B.left = (uint32_t*)(d + o_left);
+  B.items = (Item*)(d + o_items);
+  B.seq = (uint32_t*)(d + o_seq);
+  B.ctr = (unsigned long long*)(d + o_ctr);
+  B.err = (uint32_t*)(d + o_err);
+  B.total = total;
+  B.eng = batch_engine_at(d + o_eng, (uint32_t)nn);
+  B.comp = (uint32_t*)(d + o_comp);
+  B.comp_seq = (uint32_t*)(d + o_cseq);
+  B.glist = (uint32_t*)(d + o_glist);
+  B.online = 1;
+  B.n = (uint32_t)nn;
+  *out = b;
+  return SG_OK;
+}
+
 __global__ void k_batch_seed(uint32_t* seq, uint64_t init, uint64_t total, unsigned long long* ctr, uint32_t* err) {
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -497,6 +749,7 @@ __global__ void k_batch_seed(uint32_t* seq, uint64_t init, uint64_t total, unsig
     ctr[0] = 0;
     ctr[1] = init;
     ctr[2] = 0;
+    ctr[3] = 0;
     *err = 0;
   }
 }
@@ -506,9 +759,14 @@ extern "C" int sg_batch_launch(sg_batch* b, void* stream) {
   if (b->d.total == 0) return SG_OK;
   cudaStream_t st = (cudaStream_t)stream;
   const uint32_t n = b->n;
-  if (cudaMemcpyAsync(b->d.dep, b->dep0, 4ull * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(b->d.left, b->left0, 4ull * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+  if (b->online) {
+    if (batch_engine_start(b->d.eng, b->d.jobs, n, b->budget, b->granule, b->policy, st) != SG_OK ||
+        cudaMemsetAsync(b->d.comp_seq, 0, 4ull * n, st) != cudaSuccess)
+      return SG_ERR_CUDA;
+  } else if (cudaMemcpyAsync(b->d.dep, b->dep0, 4ull * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+             cudaMemcpyAsync(b->d.left, b->left0, 4ull * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
     return SG_ERR_CUDA;
+  }
   if (b->init_items &&
       cudaMemcpyAsync(b->d.items, b->items0, sizeof(Item) * b->init_items, cudaMemcpyDeviceToDevice, st) !=
           cudaSuccess)
@@ -532,6 +790,13 @@ extern "C" int sg_batch_status(sg_batch* b, uint64_t* jobs_done, uint32_t* err_f
   if (jobs_done) *jobs_done = c[2];
   if (err_flags) *err_flags = e;
   return (c[2] == b->granted && e == 0) ? SG_OK : SG_ERR_DEVICE;
+}
+
+extern "C" int sg_batch_records(sg_batch* b, sg_record* out) {
+  if (!b || !out || !b->online) return SG_ERR_INVALID;
+  if (b->n && cudaMemcpy(out, b->d.eng.rec, sizeof(sg_record) * b->n, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return SG_ERR_CUDA;
+  return SG_OK;
 }
 
 extern "C" int sg_batch_info(const sg_batch* b, uint64_t* jobs, uint64_t* chunks, uint64_t* blocks) {

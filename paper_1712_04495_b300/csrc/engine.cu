@@ -526,7 +526,89 @@ extern "C" int sg_cancel(sg_ctx* c, sg_ticket t, sg_grant* out) {
   return cancel_locked(c, t, out);
 }
 
+namespace {
+
+// Every job of a batch declared at logical time t = 0, in index order: the
+// queue holds job j at position j with its key, and one policy pass (the
+// batch kernel's first) then grants exactly what per-arrival passes would
+// (nothing is released at t = 0, so each arrival's pass grants it iff it
+// fits after the earlier grants, and first fit sees the same order).
+__global__ void k_declare_all(Eng E, const sg_job* __restrict__ jobs, uint32_t n, uint32_t policy,
+                              uint64_t granule) {
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  Sess ks{};
+  ks.policy = policy;
+  ks.granule = granule;
+  const uint64_t now = globaltimer_ns();
+  for (uint64_t j = tid; j < n; j += stride) {
+    const sg_job& jb = jobs[j];
+    const uint64_t g = round_need(jb.need, granule);
+    E.need_g[j] = g;
+    E.need_raw[j] = jb.need;
+    E.prio[j] = jb.prio;
+    E.blk_done[j] = 0;
+    E.status[j] = ST_QUEUED;
+    sg_record r;
+    r.status = ST_QUEUED; r.slot = -1; r.grant_seq = -1; r.grant_t = 0; r.offset = 0; r.done_t = 0;
+    r.arrival_t = now;
+    E.rec[j] = r;
+    E.qa[j] = (uint32_t)j;
+    E.qpos[j] = (uint32_t)j;
+    E.qt[j] = q_key(ks, g, jb.prio);
+  }
+  if (tid == 0) {
+    E.hdr->q_len = n;
+    E.hdr->q_begin = 0;
+    E.hdr->q_end = n;
+  }
+}
+
+// one level of the queue's min-tree from the level below
+__global__ void k_tree_level(uint64_t* qt, uint64_t child_off, uint64_t child_size, uint64_t parent_off,
+                             uint64_t parent_size) {
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = tid; i < parent_size; i += stride) {
+    uint64_t m = kInf;
+    for (uint64_t c = 32 * i; c < 32 * i + 32 && c < child_size; c++) {
+      const uint64_t v = qt[child_off + c];
+      m = v < m ? v : m;
+    }
+    qt[parent_off + i] = m;
+  }
+}
+
+}  // namespace
+
 namespace sg {
+// Engine state of a batch that admits on the device (batch.cu): n tickets,
+// n queue positions, the device log and a device grant ring of n entries.
+uint64_t batch_engine_bytes(uint32_t n) { return dev_layout(n, true, 4ull * n, n).total; }
+
+Eng batch_engine_at(char* base, uint32_t n) {
+  const DevLayout L = dev_layout(n, true, 4ull * n, n);
+  Eng E = eng_from(base, L);
+  E.dev_ring = (uint32_t*)(base + L.extra);
+  return E;
+}
+
+// reset to one free extent of `budget` bytes and declare all n jobs at t = 0
+int batch_engine_start(const Eng& E, const sg_job* jobs_dev, uint32_t n, uint64_t budget, uint64_t granule,
+                       uint32_t policy, cudaStream_t st) {
+  const DevLayout L = dev_layout(n, true, 4ull * n, n);
+  k_eng_reset<<<64, 256, 0, st>>>(E, budget, granule, policy, 0, n, L.qt_len);
+  if (n) k_declare_all<<<256, 256, 0, st>>>(E, jobs_dev, n, policy, granule);
+  uint64_t off = 0, size = L.qcap;
+  while (size > 32) {                    // the tree's levels, leaves first
+    const uint64_t parent = size >> 5;
+    k_tree_level<<<(unsigned)((parent + 255) / 256), 256, 0, st>>>(E.qt, off, size, off + size, parent);
+    off += size;
+    size = parent;
+  }
+  return cudaGetLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
+}
+
 cudaStream_t ctx_control_stream(sg_ctx* c) { return c->ctrl; }
 char* ctx_pool_base(sg_ctx* c) { return c->pool; }
 uint64_t ctx_pool_bytes(sg_ctx* c) { return c->pool_bytes; }

@@ -58,6 +58,7 @@ struct Eng {               // array pointers (kernel parameter, by value)
   sg_record* pub_rec;      // [cap] host-mapped copy of the log, or null
   uint32_t* pub_ring;      // [cap] host-mapped ring of granted tickets, or null
   uint32_t* pub_hdr;       // host-mapped: [0] ring tail, [1] error flags, [2] done count
+  uint32_t* dev_ring;      // [cap] device copy of the grant ring (a batch admitting on the device), or null
   uint32_t owned;          // 1: one warp owns the state for the whole kernel (replay)
 };
 
@@ -341,6 +342,10 @@ __device__ __forceinline__ void publish_record(const Eng& E, uint32_t j, const s
 
 // Append a granted ticket to the host-mapped grant ring (real runs).
 __device__ __forceinline__ void publish_grant_ring(const Eng& E, Sess& s, uint32_t j) {
+  if (E.dev_ring) {
+    if (lane_id() == 0) est(E, E.dev_ring + s.ring_tail % s.cap, j);
+    __syncwarp();
+  }
   if (E.pub_ring) {
     if (lane_id() == 0) {
       ((volatile uint32_t*)E.pub_ring)[s.ring_tail % s.cap] = j;
@@ -664,6 +669,11 @@ __device__ __forceinline__ void policy_pass(const Eng& E, Sess& s, uint64_t t, E
       const uint64_t cls = s.policy == SG_POLICY_FIFO ? 0 : q_top_class(E);
       const int64_t h = qt_find(E, s.q_begin, q_bound(s, cls, kInf));
       blocked = h >= 0 && eld(E, ng + eld(E, E.qa + h)) <= freeb;
+    } else if (s.max_ext >= freeb) {
+      // first fit (within the top class under Priority MMU) has just searched
+      // with bound min(freeb, max_ext) = freeb and found nobody: no waiter
+      // fits the byte count
+      blocked = false;
     } else if (s.policy == SG_POLICY_FIRST_FIT) {
       blocked = qt_find(E, s.q_begin, freeb) >= 0;
     } else {

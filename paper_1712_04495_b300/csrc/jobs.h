@@ -43,6 +43,11 @@ uint32_t tuned_tile(uint32_t M, uint32_t N);
 // driver entry point and kernel attributes, once (call before stream capture)
 int gemm_prepare();
 
+// engine state of a batch that admits on the device (engine.cu, batch.cu)
+uint64_t batch_engine_bytes(uint32_t n);
+Eng batch_engine_at(char* base, uint32_t n);
+int batch_engine_start(const Eng& E, const sg_job* jobs_dev, uint32_t n, uint64_t budget, uint64_t granule,
+                       uint32_t policy, cudaStream_t st);
 // a context's control stream and pool (engine.cu), for the scheduler server
 cudaStream_t ctx_control_stream(sg_ctx* c);
 char* ctx_pool_base(sg_ctx* c);

@@ -184,3 +184,41 @@ class Planned:
             self.close()
         except Exception:
             pass
+
+
+class OnlineBatch:
+    """A batch admitted on the device as it runs: the persistent grouped
+    kernel holds the batch's engine, releases each finished job's memory and
+    enqueues what the notification pass grants (no plan, no host step)."""
+
+    def __init__(self, pool: torch.Tensor, jobs: np.ndarray, tables: torch.Tensor, policy="first_fit",
+                 keep: bool = False, budget: int | None = None):
+        _require_cuda()
+        self.pool = pool
+        self.jobs = np.ascontiguousarray(jobs, dtype=tg.JOB_DTYPE)
+        self.tables = tables
+        self.budget = budget if budget is not None else pool.numel()
+        self.keep = torch.zeros(len(jobs), dtype=torch.int64, device="cuda") if keep else None
+        kp = self.keep.data_ptr() if keep else 0
+        self.batch = abi.sg_batch_build_online(pool.data_ptr(), self.budget, self.jobs, tables.data_ptr(), policy, kp)
+
+    def run(self, stream: torch.cuda.Stream | None = None) -> int:
+        return abi.sg_batch_launch(self.batch, stream_handle(stream))
+
+    def status(self):
+        return abi.sg_batch_status(self.batch)
+
+    def records(self) -> np.ndarray:
+        return abi.sg_batch_records(self.batch, len(self.jobs))
+
+    def close(self):
+        if self.batch:
+            abi.sg_batch_destroy(self.batch)
+            self.batch = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

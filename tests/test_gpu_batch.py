@@ -74,3 +74,79 @@ def test_batch_with_ragged_gemms_and_fifo():
                         np.zeros(8, np.int64), 3, (8.0,))
     tr = tg.Trace("ragged", jobs, 16 * MIB, np.stack([tg.poisson_cdf_table(8.0)]), (8.0,))
     _check_three_ways(tr, 16 * MIB, policy="fifo")
+
+
+def _online(tr, budget, policy, keep=True):
+    from paper_1712_04495_b300 import abi, runtime
+    from oracle import invariants
+    pool = torch.empty(budget, dtype=torch.uint8, device="cuda")
+    tab = runtime.device_tables(tr)
+    ob = runtime.OnlineBatch(pool, tr.jobs, tab, policy, keep=keep, budget=budget)
+    keeps = []
+    for _ in range(2):                      # launched twice: the engine is reset per launch
+        assert ob.run() == abi.SG_OK
+        torch.cuda.synchronize()
+        rc, done, err = ob.status()
+        assert (rc, err) == (abi.SG_OK, 0), (rc, done, err)
+        assert done == len(tr)
+        keeps.append(_u64(ob.keep))
+    assert np.array_equal(keeps[0], keeps[1])
+    rec = ob.records()
+    # memory safety of a real run: no overcommit, extents held at the same
+    # time are disjoint, every job granted once and finished
+    assert np.all(rec["status"] == 3)
+    assert sorted(rec["grant_seq"].tolist()) == list(range(len(tr)))
+    need_g = (tr.jobs["need"].astype(np.int64) + 255) // 256 * 256
+    ev = sorted([(int(rec["grant_t"][j]), 1, j) for j in range(len(tr))] +
+                [(int(rec["done_t"][j]), 0, j) for j in range(len(tr))])
+    used, held = 0, {}
+    for t, kind, j in ev:
+        if kind == 0:
+            used -= need_g[j]
+            held.pop(j)
+        else:
+            o = int(rec["offset"][j])
+            for k, (o2, g2) in held.items():
+                assert o + need_g[j] <= o2 or o2 + g2 <= o, (j, k)
+            held[j] = (o, int(need_g[j]))
+            used += need_g[j]
+            assert used <= budget
+    ob.close()
+    return keeps[0], pool, tab
+
+
+def test_online_batch_admits_on_the_device():
+    """The batch's own engine admits the 10,000 tiny jobs inside the
+    persistent kernel; each job's output equals the planned batch's."""
+    from paper_1712_04495_b300 import abi, runtime
+    tr = tg.trace_c4()
+    keep_online, pool, tab = _online(tr, tr.budget, "first_fit")
+    pl = runtime.Planned(pool, tr.jobs, tab, "first_fit", keep=True, budget=tr.budget, graph=False)
+    assert pl.run_batch() == abi.SG_OK
+    torch.cuda.synchronize()
+    assert np.array_equal(_u64(pl.keep), keep_online)
+    pl.close()
+    tri = np.nonzero(tr.jobs["kind"] == tg.KIND_TRIAD)[0][:16]
+    for j in tri:
+        ref = K.triad(int(tr.jobs["key"][j]), int(tr.jobs["p0"][j]))
+        assert int(keep_online[j]) == _digest_f32(ref)
+
+
+@pytest.mark.parametrize("policy", ["fifo", "prio_first_fit"])
+def test_online_batch_other_policies(policy):
+    tr = tg.trace_mixed(9, 300, None, 64 * MIB, "batch_small", triad_rng=(4096, 1 << 18),
+                        spmv_rng=(1000, 65536), gemm_set=(64, 128, 256, 512), lam=8.0)
+    jobs = tr.jobs.copy()
+    jobs["prio"] = jobs["kind"].astype(np.int64) % 2
+    tr = tg.Trace(tr.name, jobs, tr.budget, tr.tables, tr.lambdas)
+    _online(tr, 64 * MIB, policy)
+
+
+def test_online_batch_rejects_a_job_that_never_fits():
+    from paper_1712_04495_b300 import abi, runtime
+    jobs = tg.make_jobs([tg.KIND_TRIAD] * 2, [1 << 20, 1 << 20], np.zeros(2, np.int64), 1, (8.0,))
+    pool = torch.empty(4 * MIB, dtype=torch.uint8, device="cuda")
+    tab = torch.zeros(64, dtype=torch.int64, device="cuda")
+    with pytest.raises(abi.SgError):
+        abi.sg_batch_build_online(pool.data_ptr(), pool.numel(), jobs, tab.data_ptr(), "first_fit")
+
