@@ -326,8 +326,15 @@ typedef struct sg_graph sg_graph;
 int sg_graph_build(void* dev_pool, uint64_t pool_bytes, const sg_job* jobs, uint32_t n,
                    const uint64_t* tables_dev, const sg_record* plan, uint64_t* keep_dev,
                    sg_graph** out);
+/* Enqueue one run of the graph on stream (a cudaStream_t, NULL = legacy
+ * default stream); asynchronous. SG_ERR_INVALID for a NULL or unbuilt graph,
+ * SG_ERR_CUDA if the launch fails. */
 int sg_graph_launch(sg_graph* g, void* stream);
+/* Shape of the built graph: jobs in it, kernel nodes, dependency edges
+ * between jobs. Any output pointer may be NULL. SG_ERR_INVALID if g is NULL. */
 int sg_graph_info(const sg_graph* g, uint64_t* jobs, uint64_t* kernels, uint64_t* edges);
+/* Free the graph and its executable instance; g is invalid afterwards. The
+ * caller makes sure no launch of it is still running. SG_ERR_INVALID if NULL. */
 int sg_graph_destroy(sg_graph* g);
 
 /* The same plan run by one persistent grouped kernel: every job is a
@@ -346,7 +353,18 @@ typedef struct sg_batch sg_batch;
 int sg_batch_build(void* dev_pool, uint64_t pool_bytes, const sg_job* jobs, uint32_t n,
                    const uint64_t* tables_dev, const sg_record* plan, uint64_t* keep_dev,
                    sg_batch** out);
+/* Enqueue one run on stream (a cudaStream_t): the per-launch state reset
+ * (dependency counters, seeded work queue, keep_dev zeroed; for an online
+ * batch the engine re-armed) and then one cooperative launch of the
+ * persistent kernel. Asynchronous; a batch object runs one launch at a time
+ * (launches on one stream are ordered). SG_ERR_INVALID if b is NULL,
+ * SG_ERR_CUDA if a copy or the launch fails. An empty batch returns SG_OK. */
 int sg_batch_launch(sg_batch* b, void* stream);
+/* After the launch has finished (synchronises through blocking copies): the
+ * jobs that completed and the batch's error flags (SG_DEVERR_* bits, 0 =
+ * none); either pointer may be NULL.
+ * SG_OK when every planned (or, online, every declared) job finished with no
+ * flag set, SG_ERR_DEVICE otherwise, SG_ERR_CUDA if the read fails. */
 int sg_batch_status(sg_batch* b, uint64_t* jobs_done, uint32_t* err_flags);
 
 /* A batch that admits on the device instead of from a plan: the batch owns
@@ -369,6 +387,15 @@ int sg_batch_records(sg_batch* b, sg_record* out);
 int sg_batch_info(const sg_batch* b, uint64_t* jobs, uint64_t* chunks, uint64_t* workers);
 int sg_batch_destroy(sg_batch* b);
 
+/* Error flag bits, as reported by sg_device_error, sg_state, the runners'
+ * stats and sg_batch_status (0 = none). */
+#define SG_DEVERR_WAIT      1u   /* a bounded wait (engine lock, peer) gave up    */
+#define SG_DEVERR_STATE     2u   /* a ticket was in a state the operation forbids */
+#define SG_DEVERR_ORDER     4u   /* trace arrivals not in non-decreasing order    */
+#define SG_DEVERR_EVENTS    8u   /* replay event heap full                        */
+#define SG_DEVERR_NNZ      16u   /* a SpMV job generated more non-zeros than declared */
+#define SG_DEVERR_CAPACITY 32u   /* a device queue or list ran out of room        */
+#define SG_DEVERR_ITEM     64u   /* batch: a malformed work item                  */
 /* Engine error flags of the context (0 = none). */
 uint32_t sg_device_error(sg_ctx* ctx);
 
@@ -380,7 +407,12 @@ typedef struct sg_state_summary {
     uint64_t budget, used, peak_used, max_free_extent, grants, passes, frag_waits;
     uint32_t policy, free_extents, waiting, done, error_flags, reserved;
 } sg_state_summary;
+/* Fill *out (caller-owned) with the summary above. Synchronises ctx's
+ * control stream and slots first. SG_ERR_INVALID for NULL arguments,
+ * SG_ERR_CUDA if a synchronisation or the read fails. */
 int sg_state(sg_ctx* ctx, sg_state_summary* out);
+/* A static, NUL-terminated description of an SG_* code (never NULL; an
+ * unknown code gives "unrecognised code"). The caller does not free it. */
 const char* sg_strerror(int code);
 
 /* ------------------------------------------------------ job kernels */

@@ -21,6 +21,8 @@ SG_OK, SG_NOT_READY, SG_ERR_TIMEOUT, SG_ERR_TOO_LARGE, SG_ERR_INVALID, SG_ERR_CU
 SG_POLICY_FIFO, SG_POLICY_FIRST_FIT, SG_POLICY_PRIO_FIFO, SG_POLICY_PRIO_FIRST_FIT = range(4)
 POLICIES = {"fifo": 0, "first_fit": 1, "mmu": 1, "prio_fifo": 2, "prio_first_fit": 3, "prio_mmu": 3}
 SG_FLAG_FIFO_BYPASS = 1
+SG_DEVERR_WAIT, SG_DEVERR_STATE, SG_DEVERR_ORDER, SG_DEVERR_EVENTS, SG_DEVERR_NNZ, \
+    SG_DEVERR_CAPACITY, SG_DEVERR_ITEM = 1, 2, 4, 8, 16, 32, 64
 SG_ST_PENDING, SG_ST_QUEUED, SG_ST_RUNNING, SG_ST_DONE, SG_ST_TIMEOUT, SG_ST_TOO_LARGE = range(6)
 SG_RUN_SATURATED, SG_RUN_TIMED, SG_RUN_EXCLUSIVE, SG_RUN_HOST_IO, SG_RUN_KEEP = 1, 2, 4, 8, 16
 

@@ -480,7 +480,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchDev B) {
       }
     }
     if (!ok) {
-      if (g.t() == 0) atomicOr(B.err, 64u);
+      if (g.t() == 0) atomicOr(B.err, ERR_ITEM);
       break;
     }
     // completion: the worker that finishes a phase enqueues the next one; the

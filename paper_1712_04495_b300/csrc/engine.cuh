@@ -33,7 +33,11 @@ namespace sg {
 enum : uint32_t { ST_PENDING = 0, ST_QUEUED = 1, ST_RUNNING = 2, ST_DONE = 3, ST_TIMEOUT = 4,
                   ST_TOO_LARGE = 5 };
 enum : uint32_t { ERR_LOCK = 1u, ERR_STATE = 2u, ERR_ORDER = 4u, ERR_HEAP = 8u, ERR_NNZ = 16u,
-                  ERR_CAP = 32u };
+                  ERR_CAP = 32u, ERR_ITEM = 64u };
+static_assert(ERR_LOCK == SG_DEVERR_WAIT && ERR_STATE == SG_DEVERR_STATE && ERR_ORDER == SG_DEVERR_ORDER &&
+                  ERR_HEAP == SG_DEVERR_EVENTS && ERR_NNZ == SG_DEVERR_NNZ && ERR_CAP == SG_DEVERR_CAPACITY &&
+                  ERR_ITEM == SG_DEVERR_ITEM,
+              "device error bits match the ABI's SG_DEVERR_*");
 
 struct EngHdr {            // scalar state, device memory
   uint64_t budget, granule, used, seq, peak_used, frag_waits, passes;

@@ -74,3 +74,18 @@ def test_config_struct_matches_the_header():
     names = re.findall(r"\b(\w+);", body)
     assert names == [n for n, _ in abi.SgConfig._fields_]
     assert ctypes.sizeof(abi.SgConfig) == 32
+
+
+def test_binding_constants_match_the_header():
+    # every #define SG_<NAME> <integer> of the header has the same value in abi.py
+    from paper_1712_04495_b300 import abi
+    text = open(os.path.join(ROOT, "include", "schedgpu.h")).read()
+    checked = 0
+    for m in re.finditer(r"^#define\s+(SG_[A-Z0-9_]+)\s+(\d+)u?\b", text, flags=re.M):
+        name, val = m.group(1), int(m.group(2))
+        if hasattr(abi, name):
+            assert getattr(abi, name) == val, name
+            checked += 1
+    for name in ("SG_OK", "SG_ERR_DEVICE", "SG_POLICY_PRIO_FIRST_FIT", "SG_DEVERR_ITEM"):
+        assert hasattr(abi, name), name
+    assert checked >= 20
