@@ -45,6 +45,7 @@
 #include <vector>
 
 #include "../../include/schedgpu.h"
+#include "proc.h"
 
 namespace sg {
 
@@ -94,22 +95,6 @@ struct ServerCounters {
 inline uint64_t server_now_ns() {
   return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
              std::chrono::steady_clock::now().time_since_epoch()).count();
-}
-
-// Has process `pid` exited (gone, or a zombie whose resources are freed)?
-inline bool process_exited(pid_t pid) {
-  if (pid <= 0) return true;
-  if (kill(pid, 0) != 0 && errno == ESRCH) return true;
-  char path[64];
-  snprintf(path, sizeof path, "/proc/%d/stat", (int)pid);
-  FILE* f = fopen(path, "r");
-  if (!f) return true;
-  char buf[512];
-  size_t n = fread(buf, 1, sizeof buf - 1, f);
-  fclose(f);
-  buf[n] = 0;
-  const char* rp = strrchr(buf, ')');          // "pid (comm) S ..."
-  return rp && rp[1] == ' ' && (rp[2] == 'Z' || rp[2] == 'X');
 }
 
 class Server {
