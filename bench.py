@@ -423,31 +423,60 @@ def lifecycle_section(torch, abi, runtime, reps: int = 200) -> dict:
             "shutdown_us": med(t_shut), "note": "declare + wait for the grant; release + device sync"}
 
 
-def _latency_client(path: str, reps: int, q) -> None:
+class _Transport:
+    """The client calls of one of the two multi-process designs: the
+    scheduler server ("server": UNIX socket, device engine) or the shared
+    segment ("shm": host shared memory, decisions made by each client)."""
+
+    def __init__(self, a, kind: str, where: str):
+        self.a, self.kind = a, kind
+        self.h = a.sg_client_connect(where) if kind == "server" else a.sg_shm_open(where)
+
+    def pool(self):
+        return self.a.sg_client_pool(self.h) if self.kind == "server" else self.a.sg_shm_pool(self.h)
+
+    def declare(self, need: int) -> int:
+        if self.kind == "server":
+            return self.a.sg_client_declare(self.h, need, 0)
+        rc, t = self.a.sg_shm_declare(self.h, need, 0)
+        assert rc == self.a.SG_OK, rc
+        return t
+
+    def wait(self, t: int, ns: int):
+        return (self.a.sg_client_wait if self.kind == "server" else self.a.sg_shm_wait)(self.h, t, ns)
+
+    def release(self, t: int) -> int:
+        return (self.a.sg_client_release if self.kind == "server" else self.a.sg_shm_release)(self.h, t, 0)
+
+    def close(self):
+        (self.a.sg_client_close if self.kind == "server" else self.a.sg_shm_close)(self.h)
+
+
+def _latency_client(kind: str, where: str, reps: int, q) -> None:
     """Client process of `client_server_section` (no CUDA work of its own)."""
     sys.path.insert(0, ROOT)
     from paper_1712_04495_b300 import abi as a
     t0 = time.perf_counter()
-    cl = a.sg_client_connect(path)
+    cl = _Transport(a, kind, where)
     t_conn = time.perf_counter() - t0
     t_decl, t_rel = [], []
     for _ in range(reps):
         t0 = time.perf_counter()
-        tk = a.sg_client_declare(cl, 1 << 20, 0)
-        rc, _ = a.sg_client_wait(cl, tk, 10 ** 9)
+        tk = cl.declare(1 << 20)
+        rc, _ = cl.wait(tk, 10 ** 9)
         t_decl.append(time.perf_counter() - t0)
         t0 = time.perf_counter()
-        rc2 = a.sg_client_release(cl, tk, 0)
+        rc2 = cl.release(tk)
         t_rel.append(time.perf_counter() - t0)
         if rc != a.SG_OK or rc2 != a.SG_OK:
             q.put({"error": f"codes {rc} {rc2}"})
             return
-    a.sg_client_close(cl)
+    cl.close()
     med = lambda v: 1e6 * statistics.median(v)  # noqa: E731
     q.put({"connect_us": 1e6 * t_conn, "pre_allocation_us": med(t_decl), "post_free_us": med(t_rel)})
 
 
-def _serving_client(path: str, jobs: list, go, q) -> None:
+def _serving_client(kind: str, where: str, jobs: list, go, q) -> None:
     """Client process of `processes_section`: triad jobs (n, key) one after
     another on its own stream, each declared, run on the IPC-mapped grant,
     synchronised and released."""
@@ -456,8 +485,8 @@ def _serving_client(path: str, jobs: list, go, q) -> None:
     from paper_1712_04495_b300 import abi as a
     torch.cuda.set_device(0)
     torch.zeros(1, device="cuda")
-    cl = a.sg_client_connect(path)
-    a.sg_client_pool(cl)
+    cl = _Transport(a, kind, where)
+    cl.pool()
     st = torch.cuda.Stream()
     q.put(("ready", 0.0, []))
     go.wait()
@@ -465,8 +494,8 @@ def _serving_client(path: str, jobs: list, go, q) -> None:
     turn = []
     for n, key in jobs:
         t0 = time.perf_counter()
-        tk = a.sg_client_declare(cl, 12 * n)
-        rc, g = a.sg_client_wait(cl, tk, 60 * 10 ** 9)
+        tk = cl.declare(12 * n)
+        rc, g = cl.wait(tk, 60 * 10 ** 9)
         if rc != a.SG_OK:
             q.put(("error", 0.0, [rc]))
             return
@@ -474,62 +503,91 @@ def _serving_client(path: str, jobs: list, go, q) -> None:
         a.sg_gen_triad(b, c, n, key, st.cuda_stream)
         a.sg_triad(g.ptr, b, c, 3.0, n, st.cuda_stream)
         st.synchronize()
-        a.sg_client_release(cl, tk)
+        cl.release(tk)
         turn.append(time.perf_counter() - t0)
     q.put(("done", time.perf_counter() - t_start, turn))
-    a.sg_client_close(cl)
+    cl.close()
 
 
-def processes_section(torch, abi, runtime, clients: int = 4, jobs_per_client: int = 50) -> dict:
-    """The paper's setting: separate client processes sharing one GPU through
-    the scheduler (server process, UNIX socket, CUDA IPC). Triad jobs with n
-    log-uniform in [1M, 64M], all ready at once. The same jobs run in one
-    process through the trace runner, co-scheduled and exclusive-serial."""
-    import multiprocessing as mp
-    import tempfile
-    n_jobs = clients * jobs_per_client
-    tr = tg.trace_single_kind_t0(7, n_jobs, 1 << 20, 1 << 26, 16 << 30, f"triad{n_jobs}_t0_16GiB")
-    pool = torch.empty(tr.budget, dtype=torch.uint8, device="cuda")
-    sched = runtime.Scheduler(tr.budget, "first_fit", pool=pool)
-    path = os.path.join(tempfile.mkdtemp(prefix="sg_bench_"), "sock")
-    srv = abi.sg_server_start(sched.ctx, path)
-    ctx = mp.get_context("spawn")
+def _shm_name(tag: str) -> str:
+    return f"/sg_bench_{tag}_{os.getpid()}"
+
+
+def _run_clients(ctx, kind: str, where: str, work: list, timeout: float = 600):
+    """Start one client process per work list, release them together and
+    collect (wall seconds, per-job turnaround seconds)."""
     q, go = ctx.Queue(), ctx.Event()
-    work = [[] for _ in range(clients)]
-    for j in range(n_jobs):
-        work[j % clients].append((int(tr.jobs["p0"][j]), int(tr.jobs["key"][j])))
-    procs = [ctx.Process(target=_serving_client, args=(path, work[i], go, q)) for i in range(clients)]
+    procs = [ctx.Process(target=_serving_client, args=(kind, where, w, go, q)) for w in work]
     for p in procs:
         p.start()
-    out = {"workload": tr.name, "clients": clients, "jobs": n_jobs}
     try:
-        for _ in range(clients):
+        for _ in procs:
             assert q.get(timeout=300)[0] == "ready"
         t0 = time.perf_counter()
         go.set()
         turns = []
-        for _ in range(clients):
-            kind, _, turn = q.get(timeout=600)
-            assert kind == "done", (kind, turn)
+        for _ in procs:
+            kind_, _, turn = q.get(timeout=timeout)
+            assert kind_ == "done", (kind_, turn)
             turns += turn
         wall = time.perf_counter() - t0
     finally:
         for p in procs:
             p.join(60)
+    return wall, np.sort(np.array(turns))
+
+
+def processes_section(torch, abi, runtime, clients: int = 4, jobs_per_client: int = 50) -> dict:
+    """The paper's setting: separate client processes sharing one GPU through
+    the scheduler, in both designs of Sec. III: the scheduler server (UNIX
+    socket, device engine) and the shared segment (host shared memory, each
+    client decides). Clients run triad jobs with n log-uniform in [1M, 64M],
+    all ready at once, on grants in one pool mapped by CUDA IPC. The same jobs
+    run in one process through the trace runner, co-scheduled and
+    exclusive-serial."""
+    import multiprocessing as mp
+    import tempfile
+    n_jobs = clients * jobs_per_client
+    tr = tg.trace_single_kind_t0(7, n_jobs, 1 << 20, 1 << 26, 16 << 30, f"triad{n_jobs}_t0_16GiB")
+    pool = torch.empty(tr.budget, dtype=torch.uint8, device="cuda")
+    ctx = mp.get_context("spawn")
+    work = [[] for _ in range(clients)]
+    for j in range(n_jobs):
+        work[j % clients].append((int(tr.jobs["p0"][j]), int(tr.jobs["key"][j])))
+    out = {"workload": tr.name, "clients": clients, "jobs": n_jobs}
+
+    def summary(wall, turns):
+        return {"jobs_per_s": n_jobs / wall, "ms": 1e3 * wall,
+                "turnaround_p50_ms": 1e3 * float(turns[len(turns) // 2]),
+                "turnaround_p99_ms": 1e3 * float(turns[min(len(turns) - 1, int(0.99 * len(turns)))])}
+
+    sched = runtime.Scheduler(tr.budget, "first_fit", pool=pool)
+    path = os.path.join(tempfile.mkdtemp(prefix="sg_bench_"), "sock")
+    srv = abi.sg_server_start(sched.ctx, path)
+    try:
+        out["processes"] = summary(*_run_clients(ctx, "server", path, work))
+    finally:
         abi.sg_server_stop(srv)
         sched.shutdown()
-    turns = np.sort(np.array(turns))
-    out["processes"] = {"jobs_per_s": n_jobs / wall, "ms": 1e3 * wall,
-                        "turnaround_p50_ms": 1e3 * float(turns[len(turns) // 2]),
-                        "turnaround_p99_ms": 1e3 * float(turns[min(len(turns) - 1, int(0.99 * len(turns)))])}
+    name = _shm_name("proc")
+    abi.sg_shm_unlink(name)
+    h = abi.sg_shm_open(name, tr.budget, "first_fit")
+    try:
+        abi.sg_shm_set_pool(h, pool.data_ptr(), pool.numel())
+        out["processes_shared_memory"] = summary(*_run_clients(ctx, "shm", name, work))
+        st = abi.sg_shm_stats(h)
+        assert st["used"] == 0 and st["grants"] == n_jobs, st
+    finally:
+        abi.sg_shm_close(h)
+        abi.sg_shm_unlink(name)
     s = runtime.Scheduler(tr.budget, "first_fit", pool=pool)
     d_jobs, d_tab = runtime.to_device(tr.jobs), runtime.device_tables(tr)
-    for name, mode in (("one_process", abi.SG_RUN_SATURATED),
-                       ("one_process_exclusive", abi.SG_RUN_SATURATED | abi.SG_RUN_EXCLUSIVE)):
+    for nm, mode in (("one_process", abi.SG_RUN_SATURATED),
+                     ("one_process_exclusive", abi.SG_RUN_SATURATED | abi.SG_RUN_EXCLUSIVE)):
         s.run_trace(d_jobs, d_tab, mode)
         rc, _, _, st = s.run_trace(d_jobs, d_tab, mode)
         assert rc == abi.SG_OK
-        out[name] = {"jobs_per_s": n_jobs / (st["makespan_ns"] * 1e-9), "ms": st["makespan_ns"] / 1e6}
+        out[nm] = {"jobs_per_s": n_jobs / (st["makespan_ns"] * 1e-9), "ms": st["makespan_ns"] / 1e6}
     s.shutdown()
     del pool
     torch.cuda.empty_cache()
@@ -537,9 +595,10 @@ def processes_section(torch, abi, runtime, clients: int = 4, jobs_per_client: in
 
 
 def client_server_section(torch, abi, runtime, reps: int = 300) -> dict:
-    """The same life-cycle stages from a separate client process through the
-    scheduler server (UNIX socket; grants pushed by the server): the paper's
-    comparison of the library with a client-server design."""
+    """The life-cycle stages from a separate client process, in both designs
+    of Sec. III: through the scheduler server (UNIX socket; grants pushed by
+    the server) and through the shared segment (the client decides under the
+    file lock). The paper compares the two by their overhead."""
     import multiprocessing as mp
     import tempfile
     pool = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
@@ -548,7 +607,7 @@ def client_server_section(torch, abi, runtime, reps: int = 300) -> dict:
     srv = abi.sg_server_start(sched.ctx, path)
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    p = ctx.Process(target=_latency_client, args=(path, reps, q))
+    p = ctx.Process(target=_latency_client, args=("server", path, reps, q))
     p.start()
     try:
         out = q.get(timeout=300)
@@ -558,6 +617,21 @@ def client_server_section(torch, abi, runtime, reps: int = 300) -> dict:
         sched.shutdown()
     out["note"] = ("client process -> server: declare + wait for the pushed grant; "
                    "release round trip (the release kernel runs after the reply)")
+    name = _shm_name("lat")
+    abi.sg_shm_unlink(name)
+    h = abi.sg_shm_open(name, pool.numel(), "first_fit")
+    try:
+        p = ctx.Process(target=_latency_client, args=("shm", name, reps, q))
+        p.start()
+        try:
+            shm = q.get(timeout=300)
+        finally:
+            p.join(30)
+    finally:
+        abi.sg_shm_close(h)
+        abi.sg_shm_unlink(name)
+    shm["note"] = "client process on the shared segment: declare (decided in the call) + wait; release"
+    out["shared_memory"] = shm
     return out
 
 

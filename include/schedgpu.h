@@ -311,6 +311,91 @@ int sg_client_release(sg_client* c, sg_ticket t, uint64_t bytes);
  * process exits) and unmap the pool. */
 int sg_client_close(sg_client* c);
 
+/* ------------------------------------------- shared memory (no server) */
+/* The distributed control of Sec. III-A: client processes share the
+ * scheduler state (Sec. III-B) through one POSIX shared-memory segment and
+ * each makes its own admission decisions on it (pre-allocation, post-free
+ * and the policies of Sec. IV-V, the same semantics as the device engine's:
+ * strict FIFO unless SG_FLAG_FIFO_BYPASS, granule-rounded needs, address-
+ * ordered first-fit placement, so a grant is an offset in one pool).
+ * Updates are serialised by a file lock that the kernel drops when its
+ * holder dies; a waiting client sleeps on a futex in its ticket and the
+ * process that grants it wakes it. Robustness (Sec. III-A): a backup copy is
+ * written when a client closes; the structure is checked when a client opens
+ * and after a holder died inside an update, and a corrupt state is rebuilt
+ * from the ticket table, else restored from the backup, else initialised
+ * afresh; a client that closes or has been blocked for 2 ms (then every
+ * 20 ms) reclaims what processes that have exited still hold.
+ * The admission runs on the host here (the device engine needs one owner
+ * process: see sg_server_start). No call allocates device memory.
+ * Tickets are (generation << 16 | slot): a ticket that ended reads as
+ * SG_ERR_INVALID. Only the declaring process may release or withdraw it. */
+typedef struct sg_shm sg_shm;
+typedef struct sg_shm_counts {
+    uint64_t budget, granule, used, peak_used, grants, passes, frag_waits;
+    uint64_t reaped;       /* tickets reclaimed from processes that ended     */
+    uint64_t rebuilt;      /* corrupt states rebuilt from the ticket table    */
+    uint64_t restored;     /* ... restored from the backup                    */
+    uint64_t reset;        /* ... initialised afresh                          */
+    uint64_t abandoned;    /* locks taken over from a holder that died mid-update */
+    uint64_t timeouts, backups, generation;
+    uint32_t policy, max_tickets, waiting, running, free_extents, reserved;
+} sg_shm_counts;
+/* Integrity problems reported by sg_shm_check */
+#define SG_SHM_BAD_HEADER   1u
+#define SG_SHM_BAD_TICKETS  2u
+#define SG_SHM_BAD_USED     4u
+#define SG_SHM_BAD_EXTENTS  8u
+#define SG_SHM_BAD_QUEUE   16u
+#define SG_SHM_BAD_SLOTS   32u
+#define SG_SHM_DIRTY       64u   /* a holder died inside an update */
+/* Create (budget > 0, the segment does not exist) or attach to the segment
+ * `name` ("/name", POSIX shm; its backup is "/name.bak"). budget = 0 attaches
+ * only; with budget > 0 an existing segment must have the same budget,
+ * policy and granule, else SG_ERR_INVALID. cfg (may be NULL): max_tickets
+ * (tickets in use at once, 0 = 4096, <= 65536), granule, flags. SG_ERR_UNKNOWN
+ * if the segment cannot be mapped or locked within 10 s. */
+int sg_shm_open(const char* name, uint64_t budget, uint32_t policy, const sg_config* cfg, sg_shm** out);
+/* Pre-allocation: SG_OK and *out (granted at once or queued; see sg_shm_try),
+ * SG_ERR_TOO_LARGE (need > budget, not queued), SG_ERR_CAPACITY, SG_ERR_INVALID
+ * (priority outside 16 bits). */
+int sg_shm_declare(sg_shm* s, uint64_t need, int32_t priority, sg_ticket* out);
+/* Non-blocking: SG_OK (*out filled; ptr = pool + offset once the pool is
+ * mapped in this process, else NULL), SG_NOT_READY, SG_ERR_INVALID (ended). */
+int sg_shm_try(sg_shm* s, sg_ticket t, sg_grant* out);
+/* Block up to timeout_ns (UINT64_MAX = forever) for the grant. On expiry the
+ * request is withdrawn (the pass re-runs) and SG_ERR_TIMEOUT is returned,
+ * unless the grant won the race (SG_OK). */
+int sg_shm_wait(sg_shm* s, sg_ticket t, uint64_t timeout_ns, sg_grant* out);
+/* Post-free of `bytes` (0 or >= held: all, the ticket ends); a partial release
+ * keeps the granule-rounded rest at the front. SG_ERR_INVALID if t is not a
+ * running ticket of this process. The caller's work on the grant must be
+ * complete. */
+int sg_shm_release(sg_shm* s, sg_ticket t, uint64_t bytes);
+/* Snapshot of a live ticket: status, grant order, offset, grant and arrival
+ * times (CLOCK_MONOTONIC ns); slot = -1, done_t = 0. SG_ERR_INVALID if ended. */
+int sg_shm_record(sg_shm* s, sg_ticket t, sg_record* out);
+int sg_shm_stats(sg_shm* s, sg_shm_counts* out);
+/* Bytes held by process pid (the itemised used memory of Sec. III-A). */
+int sg_shm_used_by(sg_shm* s, int32_t pid, uint64_t* bytes);
+/* Run the integrity check now and recover if needed; *problems (may be
+ * NULL) gets the SG_SHM_* bits found (0 = consistent). */
+int sg_shm_check(sg_shm* s, uint32_t* problems);
+/* Publish the device pool (pool_bytes >= budget, device memory of this
+ * process) through CUDA IPC; sg_shm_pool maps it in other processes. The
+ * pool must outlive the clients' use of it; closing the publishing handle
+ * withdraws it. SG_ERR_CUDA if the handle cannot be made. */
+int sg_shm_set_pool(sg_shm* s, void* dev_pool, uint64_t pool_bytes);
+/* This process's address of the published pool: SG_OK, SG_NOT_READY (none
+ * published), SG_ERR_CUDA (cannot be mapped). The mapping lasts until close. */
+int sg_shm_pool(sg_shm* s, void** ptr);
+/* The client ends: its requests are withdrawn, its memory freed (waiters
+ * notified), the holders checked and the state backed up; then unmapped.
+ * The segment stays for the other clients. */
+int sg_shm_close(sg_shm* s);
+/* Remove the segment and its backup (clients that have it mapped keep it). */
+int sg_shm_unlink(const char* name);
+
 /* ------------------------------------------------------- batching */
 /* One CUDA graph for a whole trace: a static co-schedule. plan (host, n
  * records) is the log of sg_replay on the same jobs and pool size: it

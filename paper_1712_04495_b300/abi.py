@@ -78,6 +78,20 @@ class SgServerCounts(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class SgShmCounts(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in
+                ("budget", "granule", "used", "peak_used", "grants", "passes", "frag_waits", "reaped",
+                 "rebuilt", "restored", "reset", "abandoned", "timeouts", "backups", "generation")] + \
+               [(k, ctypes.c_uint32) for k in
+                ("policy", "max_tickets", "waiting", "running", "free_extents", "reserved")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+SG_SHM_BAD_HEADER, SG_SHM_BAD_TICKETS, SG_SHM_BAD_USED, SG_SHM_BAD_EXTENTS, SG_SHM_BAD_QUEUE, \
+    SG_SHM_BAD_SLOTS, SG_SHM_DIRTY = 1, 2, 4, 8, 16, 32, 64
+
 NO_TIMEOUT = (1 << 64) - 1
 
 
@@ -144,6 +158,19 @@ _SIGS = {
     "sg_state": ([_P, _P], ctypes.c_int),
     "sg_batch_build_online": ([_P, _U64, _P, _U32, _P, _U32, _P, ctypes.POINTER(_P)], ctypes.c_int),
     "sg_batch_records": ([_P, _P], ctypes.c_int),
+    "sg_shm_open": ([ctypes.c_char_p, _U64, _U32, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "sg_shm_declare": ([_P, _U64, ctypes.c_int32, ctypes.POINTER(_U32)], ctypes.c_int),
+    "sg_shm_try": ([_P, _U32, _P], ctypes.c_int),
+    "sg_shm_wait": ([_P, _U32, _U64, _P], ctypes.c_int),
+    "sg_shm_release": ([_P, _U32, _U64], ctypes.c_int),
+    "sg_shm_record": ([_P, _U32, _P], ctypes.c_int),
+    "sg_shm_stats": ([_P, _P], ctypes.c_int),
+    "sg_shm_used_by": ([_P, ctypes.c_int32, ctypes.POINTER(_U64)], ctypes.c_int),
+    "sg_shm_check": ([_P, ctypes.POINTER(_U32)], ctypes.c_int),
+    "sg_shm_set_pool": ([_P, _P, _U64], ctypes.c_int),
+    "sg_shm_pool": ([_P, ctypes.POINTER(_P)], ctypes.c_int),
+    "sg_shm_close": ([_P], ctypes.c_int),
+    "sg_shm_unlink": ([ctypes.c_char_p], ctypes.c_int),
 }
 
 _lib = None
@@ -482,3 +509,81 @@ def sg_gen_gemm(A, Bt, M: int, N: int, K: int, key: int, stream: int = 0) -> int
 
 def sg_digest(ptr, words: int, out_ptr, stream: int = 0) -> int:
     return lib().sg_digest(ptr, words, out_ptr, stream)
+
+
+# ------------------------------------------------ shared memory (no server)
+def sg_shm_open(name: str, budget: int = 0, policy="first_fit", max_tickets: int = 0, granule: int = 0,
+                flags: int = 0) -> int:
+    """Create (budget > 0) or attach to (budget 0) the shared segment `name`."""
+    pol = POLICIES[policy] if isinstance(policy, str) else int(policy)
+    cfg = SgConfig(policy=pol, flags=flags, max_tickets=max_tickets, granule=granule)
+    out = _P()
+    _check(lib().sg_shm_open(name.encode(), budget, pol, ctypes.byref(cfg), ctypes.byref(out)), "sg_shm_open")
+    return out.value
+
+
+def sg_shm_declare(h: int, need: int, priority: int = 0):
+    """(rc, ticket): rc is SG_OK or the refusal (SG_ERR_TOO_LARGE, ...)."""
+    t = _U32()
+    rc = lib().sg_shm_declare(h, need, priority, ctypes.byref(t))
+    return rc, (t.value if rc == SG_OK else None)
+
+
+def sg_shm_try(h: int, ticket: int):
+    g = SgGrant()
+    rc = lib().sg_shm_try(h, ticket, ctypes.byref(g))
+    return rc, (g if rc == SG_OK else None)
+
+
+def sg_shm_wait(h: int, ticket: int, timeout_ns: int = NO_TIMEOUT):
+    g = SgGrant()
+    rc = lib().sg_shm_wait(h, ticket, timeout_ns, ctypes.byref(g))
+    return rc, (g if rc == SG_OK else None)
+
+
+def sg_shm_release(h: int, ticket: int, nbytes: int = 0) -> int:
+    return lib().sg_shm_release(h, ticket, nbytes)
+
+
+def sg_shm_record(h: int, ticket: int):
+    """(rc, record): record is a RECORD_DTYPE scalar while the ticket lives."""
+    r = np.zeros(1, dtype=RECORD_DTYPE)
+    rc = lib().sg_shm_record(h, ticket, r.ctypes.data_as(_P))
+    return rc, (r[0] if rc == SG_OK else None)
+
+
+def sg_shm_stats(h: int) -> dict:
+    c = SgShmCounts()
+    _check(lib().sg_shm_stats(h, ctypes.byref(c)), "sg_shm_stats")
+    return c.as_dict()
+
+
+def sg_shm_used_by(h: int, pid: int) -> int:
+    b = _U64()
+    _check(lib().sg_shm_used_by(h, pid, ctypes.byref(b)), "sg_shm_used_by")
+    return b.value
+
+
+def sg_shm_check(h: int) -> int:
+    """Integrity check (and recovery); the SG_SHM_* problems found."""
+    p = _U32()
+    _check(lib().sg_shm_check(h, ctypes.byref(p)), "sg_shm_check")
+    return p.value
+
+
+def sg_shm_set_pool(h: int, dev_ptr: int, pool_bytes: int):
+    _check(lib().sg_shm_set_pool(h, dev_ptr, pool_bytes), "sg_shm_set_pool")
+
+
+def sg_shm_pool(h: int) -> int:
+    p = _P()
+    _check(lib().sg_shm_pool(h, ctypes.byref(p)), "sg_shm_pool")
+    return p.value
+
+
+def sg_shm_close(h: int):
+    _check(lib().sg_shm_close(h), "sg_shm_close")
+
+
+def sg_shm_unlink(name: str) -> int:
+    return lib().sg_shm_unlink(name.encode())

@@ -47,6 +47,7 @@
 #include <algorithm>
 #include <atomic>
 #include <climits>
+#include <cstddef>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -64,8 +65,9 @@ constexpr uint32_t kFree = 0xffffffffu;     // status of an unused ticket slot
 
 // integrity problems (sg_shm_check)
 enum : uint32_t {
-  BAD_HEADER = 1u, BAD_TICKETS = 2u, BAD_USED = 4u, BAD_EXTENTS = 8u, BAD_QUEUE = 16u, BAD_SLOTS = 32u,
-  DIRTY = 64u
+  BAD_HEADER = SG_SHM_BAD_HEADER, BAD_TICKETS = SG_SHM_BAD_TICKETS, BAD_USED = SG_SHM_BAD_USED,
+  BAD_EXTENTS = SG_SHM_BAD_EXTENTS, BAD_QUEUE = SG_SHM_BAD_QUEUE, BAD_SLOTS = SG_SHM_BAD_SLOTS,
+  DIRTY = SG_SHM_DIRTY
 };
 
 struct Hdr {
@@ -85,7 +87,8 @@ struct Hdr {
   int32_t pool_pid;
   uint64_t pool_pid_start, pool_offset, pool_bytes, pool_local;
   uint8_t pool_handle[64];
-  uint64_t reserved[8];
+  uint64_t pool_owner;          // the handle that published it
+  uint64_t reserved[7];
 };
 
 struct Tk {
@@ -98,6 +101,11 @@ struct Tk {
   uint64_t arrival_seq, arrival_ns;
 };
 static_assert(std::atomic<uint32_t>::is_always_lock_free, "futex word");
+// The segment is a wire format between processes (and the host-side tests
+// that damage it on purpose): these offsets are fixed.
+static_assert(sizeof(Hdr) == 344 && offsetof(Hdr, dirty) == 48 && offsetof(Hdr, used) == 64, "header layout");
+static_assert(sizeof(Tk) == 88 && offsetof(Tk, pid) == 8 && offsetof(Tk, need_g) == 40 && offsetof(Tk, offset) == 48,
+              "ticket layout");
 
 inline uint64_t align64(uint64_t x) { return (x + 63) & ~63ull; }
 
