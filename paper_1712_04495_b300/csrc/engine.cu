@@ -25,11 +25,6 @@ using namespace sg;
 namespace {
 
 // ------------------------------------------------------------- kernels
-__device__ __forceinline__ uint64_t round_need(uint64_t need, uint64_t granule) {
-  uint64_t g = (need + granule - 1) / granule * granule;
-  return g == 0 ? granule : g;
-}
-
 __global__ void k_eng_reset(Eng E, uint64_t budget, uint64_t granule, uint32_t policy, uint32_t flags,
                             uint32_t cap, uint64_t qt_len) {
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -112,55 +107,7 @@ __global__ void k_cancel(Eng shared, uint32_t t) {
 __global__ void k_replay(Eng state, const sg_job* __restrict__ jobs, uint32_t n, uint32_t exclusive,
                          uint64_t* dur, uint64_t* tmo, EvHeap H, uint64_t* stats) {
   if (threadIdx.x >= 32) return;
-  const Eng E = eng_owned(state);   // this warp is the only user of the state
-  const uint32_t lane = lane_id();
-  const EngHdr* h0 = E.hdr;
-  const uint64_t budget = h0->budget, granule = h0->granule;
-  uint32_t bad = 0;
-  for (uint32_t j = lane; j < n; j += 32) {
-    const sg_job& jb = jobs[j];
-    uint64_t g = exclusive ? budget : round_need(jb.need, granule);
-    E.need_g[j] = g;
-    E.need_raw[j] = exclusive ? budget : jb.need;
-    E.prio[j] = jb.prio;
-    E.status[j] = ST_PENDING;
-    dur[j] = jb.duration_ns;
-    tmo[j] = jb.timeout_ns;
-    sg_record r;
-    r.status = ST_PENDING; r.slot = -1; r.grant_seq = -1; r.grant_t = 0; r.offset = 0;
-    r.done_t = 0; r.arrival_t = jb.arrival_ns;
-    E.rec[j] = r;
-    if (j > 0 && jobs[j - 1].arrival_ns > jb.arrival_ns) bad = 1;
-  }
-  __syncwarp();
-  Sess s = sess_load(E);
-  if (__any_sync(SG_FULL, bad)) s.err |= ERR_ORDER;
-  uint32_t na = 0;
-  while (s.err == 0) {
-    bool has_a = na < n;
-    bool has_e = H.n > 0;
-    if (!has_a && !has_e) break;
-    uint64_t et = 0, ek = 0, at = 0, ak = 0;
-    if (has_e) { et = H.t[0]; ek = H.k[0]; }
-    if (has_a) { at = jobs[na].arrival_ns; ak = ((uint64_t)EV_ARRIVE << 32) | na; }
-    bool take_e = has_e && (!has_a || ev_less(et, ek, at, ak));
-    if (take_e) {
-      heap_pop(H);
-      uint32_t type = (uint32_t)(ek >> 32), j = (uint32_t)ek;
-      if (type == EV_COMPLETE) op_release(E, s, j, 0, et, &H, dur);
-      else op_cancel(E, s, j, et, &H, dur);
-    } else {
-      op_declare(E, s, na, at, -1, &H, dur, tmo);
-      na++;
-    }
-  }
-  sess_store(E, s);
-  if (stats && lane == 0) {
-    stats[0] = s.peak;
-    stats[1] = s.frag;
-    stats[2] = s.passes;
-    stats[3] = s.err | ldcg(&E.hdr->err);
-  }
+  replay_run(state, jobs, n, exclusive, dur, tmo, H, stats);
 }
 
 // ------------------------------------------------------- device layout
@@ -704,7 +651,7 @@ extern "C" int sg_run_trace(sg_ctx* c, const sg_job* jobs, uint32_t n, const uin
   std::vector<uint32_t> pending, pend_hp;
   pending.reserve(n);
   pend_hp.reserve(n);
-  uint32_t ring_head = 0, failed = 0;
+  uint32_t ring_head = 0, failed = 0, bad_grants = 0;
   CK(cudaEventRecord(c->ev0, c->ctrl));
   uint32_t declared = 0;
   const uint64_t t0 = now_ns();
@@ -756,9 +703,16 @@ extern "C" int sg_run_trace(sg_ctx* c, const sg_job* jobs, uint32_t n, const uin
         h.eng = c->eng;
         h.ticket = t;
         h.active = 1;
-        char* base = c->pool + c->h_rec[t].offset;
-        int lrc = launch_job(hj[t], base, tables_dev, h, want_keep ? c->d_keep + t : nullptr, c->d_err,
-                             c->slots[slot], &launches);
+        // a grant outside the pool is never run on (the engine flags its own
+        // inconsistencies; this keeps a job from writing outside the pool)
+        const uint64_t off = c->h_rec[t].offset;
+        const uint64_t need_g = (hj[t].need + c->granule - 1) / c->granule * c->granule;
+        int lrc = SG_ERR_DEVICE;
+        if (off <= c->budget && need_g <= c->budget - off)
+          lrc = launch_job(hj[t], c->pool + off, tables_dev, h, want_keep ? c->d_keep + t : nullptr, c->d_err,
+                           c->slots[slot], &launches);
+        else
+          bad_grants++;
         if (lrc != SG_OK) {
           // the job cannot run: give its memory back so no waiter is lost
           cudaGetLastError();
@@ -836,7 +790,7 @@ extern "C" int sg_run_trace(sg_ctx* c, const sg_job* jobs, uint32_t n, const uin
     stats->jobs_done = n_done;
     stats->jobs_failed = n_bad + failed;
   }
-  if (err || derr) return SG_ERR_DEVICE;
+  if (err || derr || bad_grants) return SG_ERR_DEVICE;
   if (n_done + failed < n && n_bad > 0) return failed ? SG_ERR_INVALID : SG_ERR_DEVICE;
   return failed ? SG_ERR_INVALID : SG_OK;
 }

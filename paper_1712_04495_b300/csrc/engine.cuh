@@ -77,6 +77,12 @@ __device__ __forceinline__ void est(const Eng& E, T* p, T v) {
   else stcg(p, v);
 }
 
+// granule-rounded request; a request of 0 bytes still takes a granule
+__device__ __forceinline__ uint64_t round_need(uint64_t need, uint64_t granule) {
+  uint64_t g = (need + granule - 1) / granule * granule;
+  return g == 0 ? granule : g;
+}
+
 // Lane-uniform register copy of the scalar state for one locked session.
 struct Sess {
   uint64_t budget, granule, used, seq, peak, frag, passes, max_ext;
@@ -376,21 +382,27 @@ __device__ __forceinline__ bool ev_less(uint64_t ta, uint64_t ka, uint64_t tb, u
   return ta < tb || (ta == tb && ka < kb);
 }
 
+// A 4-ary min-heap on (time, key), kept by lane 0. Entries move into a hole
+// and the moving entry stays in registers, so no step reloads what it has
+// just stored (a load right behind a store to the same line waits for it).
+// Keys are unique (they carry the ticket), so the pop order is the same for
+// any correct heap.
 __device__ __forceinline__ void heap_push(EvHeap& H, uint64_t t, uint64_t k, Sess& s) {
   if (lane_id() == 0) {
     if (H.n >= H.cap) {
       s.err |= ERR_HEAP;
     } else {
       uint32_t i = H.n++;
-      H.t[i] = t;
-      H.k[i] = k;
       while (i > 0) {
-        uint32_t p = (i - 1) / 2;
-        if (!ev_less(H.t[i], H.k[i], H.t[p], H.k[p])) break;
-        uint64_t tt = H.t[i], kk = H.k[i];
-        H.t[i] = H.t[p]; H.k[i] = H.k[p]; H.t[p] = tt; H.k[p] = kk;
+        const uint32_t p = (i - 1) / 4;
+        const uint64_t pt = H.t[p], pk = H.k[p];
+        if (!ev_less(t, k, pt, pk)) break;
+        H.t[i] = pt;
+        H.k[i] = pk;
         i = p;
       }
+      H.t[i] = t;
+      H.k[i] = k;
     }
   }
   H.n = __shfl_sync(SG_FULL, H.n, 0);
@@ -399,20 +411,31 @@ __device__ __forceinline__ void heap_push(EvHeap& H, uint64_t t, uint64_t k, Ses
 }
 
 __device__ __forceinline__ void heap_pop(EvHeap& H) {
+  __syncwarp();                                   // every lane has read the top before lane 0 moves it
   if (lane_id() == 0) {
-    uint32_t n = --H.n;
-    H.t[0] = H.t[n];
-    H.k[0] = H.k[n];
+    const uint32_t n = --H.n;
+    const uint64_t xt = H.t[n], xk = H.k[n];      // the last entry sinks from the root
     uint32_t i = 0;
     for (;;) {
-      uint32_t l = 2 * i + 1, r = l + 1, m = i;
-      if (l < n && ev_less(H.t[l], H.k[l], H.t[m], H.k[m])) m = l;
-      if (r < n && ev_less(H.t[r], H.k[r], H.t[m], H.k[m])) m = r;
-      if (m == i) break;
-      uint64_t tt = H.t[i], kk = H.k[i];
-      H.t[i] = H.t[m]; H.k[i] = H.k[m]; H.t[m] = tt; H.k[m] = kk;
-      i = m;
+      const uint32_t c0 = 4 * i + 1;
+      if (c0 >= n) break;
+      uint64_t ct[4], ck[4];
+#pragma unroll
+      for (uint32_t c = 0; c < 4; c++) {
+        ct[c] = c0 + c < n ? H.t[c0 + c] : ~0ull;
+        ck[c] = c0 + c < n ? H.k[c0 + c] : ~0ull;
+      }
+      uint32_t m = 0;
+#pragma unroll
+      for (uint32_t c = 1; c < 4; c++)
+        if (c0 + c < n && ev_less(ct[c], ck[c], ct[m], ck[m])) m = c;
+      if (!ev_less(ct[m], ck[m], xt, xk)) break;
+      H.t[i] = ct[m];
+      H.k[i] = ck[m];
+      i = c0 + m;
     }
+    H.t[i] = xt;
+    H.k[i] = xk;
   }
   H.n = __shfl_sync(SG_FULL, H.n, 0);
   __syncwarp();
@@ -776,6 +799,64 @@ __device__ __forceinline__ uint32_t op_cancel(const Eng& E, Sess& s, uint32_t j,
   // removing the head can unblock FIFO: notify
   policy_pass(E, s, t, heap, dur);
   return ST_TIMEOUT;
+}
+
+// Replay of a trace by one warp on a logical clock: the whole event loop
+// (arrivals in index order, completions at grant + declared duration,
+// timeouts), one policy pass per event. Events at equal time: completions,
+// then arrivals, then timeouts, then by ticket.
+__device__ __forceinline__ void replay_run(const Eng& state, const sg_job* __restrict__ jobs, uint32_t n,
+                                           uint32_t exclusive, uint64_t* dur, uint64_t* tmo, EvHeap& H,
+                                           uint64_t* stats) {
+  const Eng E = eng_owned(state);   // this warp is the only user of the state
+  const uint32_t lane = lane_id();
+  const EngHdr* h0 = E.hdr;
+  const uint64_t budget = h0->budget, granule = h0->granule;
+  uint32_t bad = 0;
+  for (uint32_t j = lane; j < n; j += 32) {
+    const sg_job& jb = jobs[j];
+    uint64_t g = exclusive ? budget : round_need(jb.need, granule);
+    E.need_g[j] = g;
+    E.need_raw[j] = exclusive ? budget : jb.need;
+    E.prio[j] = jb.prio;
+    E.status[j] = ST_PENDING;
+    dur[j] = jb.duration_ns;
+    tmo[j] = jb.timeout_ns;
+    sg_record r;
+    r.status = ST_PENDING; r.slot = -1; r.grant_seq = -1; r.grant_t = 0; r.offset = 0;
+    r.done_t = 0; r.arrival_t = jb.arrival_ns;
+    E.rec[j] = r;
+    if (j > 0 && jobs[j - 1].arrival_ns > jb.arrival_ns) bad = 1;
+  }
+  __syncwarp();
+  Sess s = sess_load(E);
+  if (__any_sync(SG_FULL, bad)) s.err |= ERR_ORDER;
+  uint32_t na = 0;
+  while (s.err == 0) {
+    bool has_a = na < n;
+    bool has_e = H.n > 0;
+    if (!has_a && !has_e) break;
+    uint64_t et = 0, ek = 0, at = 0, ak = 0;
+    if (has_e) { et = H.t[0]; ek = H.k[0]; }
+    if (has_a) { at = jobs[na].arrival_ns; ak = ((uint64_t)EV_ARRIVE << 32) | na; }
+    bool take_e = has_e && (!has_a || ev_less(et, ek, at, ak));
+    if (take_e) {
+      heap_pop(H);
+      uint32_t type = (uint32_t)(ek >> 32), j = (uint32_t)ek;
+      if (type == EV_COMPLETE) op_release(E, s, j, 0, et, &H, dur);
+      else op_cancel(E, s, j, et, &H, dur);
+    } else {
+      op_declare(E, s, na, at, -1, &H, dur, tmo);
+      na++;
+    }
+  }
+  sess_store(E, s);
+  if (stats && lane == 0) {
+    stats[0] = s.peak;
+    stats[1] = s.frag;
+    stats[2] = s.passes;
+    stats[3] = s.err | ldcg(&E.hdr->err);
+  }
 }
 
 // Locked release from a job kernel's last block (warp 0 of it).
