@@ -372,23 +372,28 @@ def batching_section(torch, abi, runtime, reps: int = 3) -> dict:
     return out
 
 
-def serving_section(torch, abi, runtime, requests: int, rates=(1000, 2000, 5000, 10000, 20000)) -> dict:
+def serving_section(torch, abi, runtime, requests: int, rates=(1000, 2000, 5000, 10000, 20000),
+                    overlap_rates=(5000, 10000)) -> dict:
     """Open-loop serving: Poisson arrivals at each rate, the mixed size mix,
     64 GiB pool, first fit; requests are declared at their arrival time and
-    admitted as memory frees up while earlier ones run."""
-    out = {"requests_per_rate": requests, "pool_gib": 64, "policy": "first_fit", "rates": {}}
-    s = runtime.Scheduler(64 << 30, "first_fit")
-    for r in rates:
-        tr = tg.trace_c5(n_jobs=requests, rate_per_s=float(r))
-        rc, _, _, st = s.run_trace(runtime.to_device(tr.jobs), runtime.device_tables(tr), abi.SG_RUN_TIMED)
-        assert rc == abi.SG_OK, st
-        out["rates"][str(r)] = {
-            "jobs_per_s": requests / (st["makespan_ns"] * 1e-9),
-            "wait_p50_ms": st["wait_p50_ns"] / 1e6, "wait_p99_ms": st["wait_p99_ns"] / 1e6,
-            "turnaround_p50_ms": st["turnaround_p50_ns"] / 1e6,
-            "turnaround_p99_ms": st["turnaround_p99_ns"] / 1e6,
-            "makespan_ms": st["makespan_ns"] / 1e6, "peak_used_gib": st["peak_used"] / 2 ** 30}
-    s.shutdown()
+    admitted as memory frees up while earlier ones run. `overlap` repeats some
+    rates with the runner starting SpMV and GEMM jobs side by side."""
+    out = {"requests_per_rate": requests, "pool_gib": 64, "policy": "first_fit", "rates": {}, "overlap": {}}
+    pool = torch.empty(64 << 30, dtype=torch.uint8, device="cuda")
+    for run_flags, rs, key in ((0, rates, "rates"), (abi.SG_RUNF_OVERLAP, overlap_rates, "overlap")):
+        s = runtime.Scheduler(64 << 30, "first_fit", pool=pool, run_flags=run_flags)
+        for r in rs:
+            tr = tg.trace_c5(n_jobs=requests, rate_per_s=float(r))
+            rc, _, _, st = s.run_trace(runtime.to_device(tr.jobs), runtime.device_tables(tr), abi.SG_RUN_TIMED)
+            assert rc == abi.SG_OK, st
+            out[key][str(r)] = {
+                "jobs_per_s": requests / (st["makespan_ns"] * 1e-9),
+                "wait_p50_ms": st["wait_p50_ns"] / 1e6, "wait_p99_ms": st["wait_p99_ns"] / 1e6,
+                "turnaround_p50_ms": st["turnaround_p50_ns"] / 1e6,
+                "turnaround_p99_ms": st["turnaround_p99_ns"] / 1e6,
+                "makespan_ms": st["makespan_ns"] / 1e6, "peak_used_gib": st["peak_used"] / 2 ** 30}
+        s.shutdown()
+    del pool
     torch.cuda.empty_cache()
     return out
 
@@ -697,6 +702,7 @@ def kinds_section(torch, abi, runtime, reps: int = 3) -> dict:
     tr = tg.trace_c2(saturated=True)
     tab = runtime.device_tables(tr)
     s = runtime.Scheduler(tr.budget, "first_fit")
+    ov = runtime.Scheduler(tr.budget, "first_fit", pool=s.pool, run_flags=abi.SG_RUNF_OVERLAP)
     out = {}
     for kinds in ((tg.KIND_TRIAD,), (tg.KIND_SPMV,), (tg.KIND_GEMM,), (tg.KIND_TRIAD, tg.KIND_SPMV),
                   (tg.KIND_TRIAD, tg.KIND_GEMM), (tg.KIND_SPMV, tg.KIND_GEMM),
@@ -704,16 +710,23 @@ def kinds_section(torch, abi, runtime, reps: int = 3) -> dict:
         jobs = tr.jobs[np.isin(tr.jobs["kind"], kinds)].copy()
         d = runtime.to_device(jobs)
         ms = {}
-        for name, mode in (("co", abi.SG_RUN_SATURATED), ("exclusive", abi.SG_RUN_SATURATED | abi.SG_RUN_EXCLUSIVE)):
+        both = tg.KIND_SPMV in kinds and tg.KIND_GEMM in kinds
+        for name, sch, mode in (("co", s, abi.SG_RUN_SATURATED), ("overlap", ov, abi.SG_RUN_SATURATED),
+                                ("exclusive", s, abi.SG_RUN_SATURATED | abi.SG_RUN_EXCLUSIVE)):
+            if name == "overlap" and not both:
+                continue   # the start rule only separates SpMV from GEMM
             t = []
             for _ in range(reps):
-                rc, _, _, st = s.run_trace(d, tab, mode)
+                rc, _, _, st = sch.run_trace(d, tab, mode)
                 assert rc == abi.SG_OK
                 t.append(st["makespan_ns"] / 1e6)
             ms[name] = statistics.median(t)
-        out["+".join(tg.KIND_NAMES[k] for k in kinds)] = {
-            "jobs": len(jobs), "co_ms": ms["co"], "exclusive_ms": ms["exclusive"],
-            "ratio": ms["co"] / ms["exclusive"]}
+        row = {"jobs": len(jobs), "co_ms": ms["co"], "exclusive_ms": ms["exclusive"],
+               "ratio": ms["co"] / ms["exclusive"]}
+        if both:
+            row["overlap_ms"] = ms["overlap"]
+        out["+".join(tg.KIND_NAMES[k] for k in kinds)] = row
+    ov.shutdown()
     s.shutdown()
     return out
 
@@ -818,10 +831,16 @@ def main():
         sched_fifo = [step(s=fifo) for _ in range(2)]
         fifo.shutdown()
         ms["fifo"] = statistics.median(s["makespan_ns"] for s in sched_fifo) / 1e6
+        # the runner starting SpMV and GEMM jobs side by side (SG_RUNF_OVERLAP)
+        for name, pol in (("first_fit_overlap", "first_fit"), ("fifo_overlap", "fifo")):
+            ov = runtime.Scheduler(trace.budget, pol, pool=sched.pool, run_flags=abi.SG_RUNF_OVERLAP)
+            ms[name] = statistics.median(step(s=ov)["makespan_ns"] for _ in range(3)) / 1e6
+            ov.shutdown()
         ser = [step(abi.SG_RUN_SATURATED | abi.SG_RUN_EXCLUSIVE) for _ in range(2)]
         ms["exclusive_serial"] = statistics.median(s["makespan_ns"] for s in ser) / 1e6
         extra["makespan_ms"] = ms
-        extra["makespan_ratio_vs_serial"] = {k: ms[k] / ms["exclusive_serial"] for k in ("first_fit", "fifo")}
+        extra["makespan_ratio_vs_serial"] = {k: ms[k] / ms["exclusive_serial"] for k in
+                                             ("first_fit", "fifo", "first_fit_overlap", "fifo_overlap")}
         extra["wait_p50_ms"] = statistics.median(s["wait_p50_ns"] for s in stats) / 1e6
         extra["wait_p99_ms"] = statistics.median(s["wait_p99_ns"] for s in stats) / 1e6
         extra["turnaround_p99_ms"] = statistics.median(s["turnaround_p99_ns"] for s in stats) / 1e6
@@ -882,6 +901,8 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD + "_t0", "jobs": n, "pool_gib": 16, "policy": "first_fit",
                            "arrivals": "t=0 (saturated)", "seed": 0,
+                           "start_rule": "SpMV and GEMM jobs in alternating phases (<= 64 starts), "
+                                         "triads beside either; stream slots 4 + 4 GEMM",
                            "l2": "inputs larger than L2 (about 50 GB of job data per step)",
                            "parallelism": f"replicas x{ws}"},
                 "gpu_launches": launches, "clocks": clocks, "wall_s": wall,

@@ -105,8 +105,22 @@ typedef struct sg_config {
     uint32_t n_streams;    /* stream slots for sg_run_trace's non-GEMM jobs (0 = 4) */
     uint64_t granule;      /* allocation granule, power of two >= 256 (0 = 256) */
     uint32_t n_gemm_streams; /* high-priority slots for GEMM jobs (0 = 4)  */
-    uint32_t reserved;     /* 0 */
+    uint16_t run_flags;    /* SG_RUNF_*: when sg_run_trace starts admitted jobs (0 = default) */
+    uint16_t phase_jobs;   /* starts of one kind per SpMV / GEMM phase while the other kind waits (0 = 64) */
 } sg_config;
+
+/* sg_config.run_flags. By default sg_run_trace never runs an SpMV job and a
+ * GEMM job at the same time: it alternates phases of the two kinds, and
+ * triads run beside either. A phase ends when its kind has no admitted job
+ * left to start, or after phase_jobs starts while the other kind has
+ * admitted jobs waiting; the next phase starts once the last job of the
+ * previous one has finished. Admission is decided as before (the policy
+ * pass and the placement); the rule only decides when an admitted job
+ * starts, which in a real run moves its release and so later grants. On B300 an SpMV's random gathers and a GEMM's operand stream
+ * both load L2; on the mixed trace, running the two kinds in turn finishes
+ * sooner and with a shorter tail turnaround under load than overlapping
+ * them. SG_RUNF_OVERLAP starts every admitted job as soon as a slot frees. */
+#define SG_RUNF_OVERLAP  1u
 
 typedef struct sg_grant {
     uint64_t offset;       /* byte offset in the pool                      */

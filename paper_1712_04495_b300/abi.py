@@ -25,6 +25,7 @@ SG_DEVERR_WAIT, SG_DEVERR_STATE, SG_DEVERR_ORDER, SG_DEVERR_EVENTS, SG_DEVERR_NN
     SG_DEVERR_CAPACITY, SG_DEVERR_ITEM = 1, 2, 4, 8, 16, 32, 64
 SG_ST_PENDING, SG_ST_QUEUED, SG_ST_RUNNING, SG_ST_DONE, SG_ST_TIMEOUT, SG_ST_TOO_LARGE = range(6)
 SG_RUN_SATURATED, SG_RUN_TIMED, SG_RUN_EXCLUSIVE, SG_RUN_HOST_IO, SG_RUN_KEEP = 1, 2, 4, 8, 16
+SG_RUNF_OVERLAP = 1
 
 JOB_DTYPE = _tg.JOB_DTYPE
 RECORD_DTYPE = np.dtype([("status", "<i4"), ("slot", "<i4"), ("grant_seq", "<i8"),
@@ -37,7 +38,7 @@ class SgConfig(ctypes.Structure):
     _fields_ = [("policy", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("max_tickets", ctypes.c_uint32), ("n_streams", ctypes.c_uint32),
                 ("granule", ctypes.c_uint64), ("n_gemm_streams", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("run_flags", ctypes.c_uint16), ("phase_jobs", ctypes.c_uint16)]
 
 
 class SgGrant(ctypes.Structure):
@@ -208,9 +209,9 @@ def sg_strerror(code: int) -> str:
 
 # ------------------------------------------------------------- life cycle
 def sg_init(pool_ptr: int, pool_bytes: int, policy=0, flags=0, max_tickets=0, n_streams=0,
-            granule=0, n_gemm_streams=0) -> int:
+            granule=0, n_gemm_streams=0, run_flags=0, phase_jobs=0) -> int:
     pol = POLICIES[policy] if isinstance(policy, str) else int(policy)
-    cfg = SgConfig(pol, flags, max_tickets, n_streams, granule, n_gemm_streams, 0)
+    cfg = SgConfig(pol, flags, max_tickets, n_streams, granule, n_gemm_streams, run_flags, phase_jobs)
     out = _P()
     _check(lib().sg_init(ctypes.byref(out), pool_ptr, pool_bytes, ctypes.byref(cfg)), "sg_init")
     return out.value

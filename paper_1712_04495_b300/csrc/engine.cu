@@ -19,10 +19,18 @@
 
 #include "engine.cuh"
 #include "jobs.h"
+#include "phases.h"
 
 using namespace sg;
 
+static_assert(kKindTriad == SG_KIND_TRIAD && kKindSpmv == SG_KIND_SPMV && kKindGemm == SG_KIND_GEMM,
+              "runner kinds follow the ABI's job kinds");
+
 namespace {
+
+// the runner's queue of a job kind (unknown kinds go with the triads; their
+// launch fails and their memory is given back)
+inline int kind_of(const sg_job& j) { return j.kind < kKinds ? (int)j.kind : kKindTriad; }
 
 // ------------------------------------------------------------- kernels
 __global__ void k_eng_reset(Eng E, uint64_t budget, uint64_t granule, uint32_t policy, uint32_t flags,
@@ -225,6 +233,8 @@ struct sg_ctx {
   std::vector<uint8_t> in_free;
   cudaStream_t ctrl = nullptr;
   uint32_t n_hp = 4;             // high-priority slots [n_slots, n_slots + n_hp): GEMM jobs
+  uint32_t run_flags = 0;        // SG_RUNF_*
+  uint32_t phase_jobs = 64;      // starts of one kind per SpMV / GEMM phase (phases.h)
   std::vector<cudaStream_t> slots;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<cudaEvent_t> slot_ev;
@@ -282,6 +292,7 @@ extern "C" int sg_init(sg_ctx** out, void* dev_pool, uint64_t pool_bytes, const 
   uint32_t cap = d.max_tickets ? d.max_tickets : (1u << 17);
   if (cap > (1u << 24)) return SG_ERR_INVALID;
   if (d.n_streams > 1024 || d.n_gemm_streams > 1024) return SG_ERR_INVALID;
+  if (d.run_flags & ~SG_RUNF_OVERLAP) return SG_ERR_INVALID;
   sg_ctx* c = new sg_ctx();
   c->pool = (char*)dev_pool;
   c->pool_bytes = pool_bytes;
@@ -295,6 +306,8 @@ extern "C" int sg_init(sg_ctx** out, void* dev_pool, uint64_t pool_bytes, const 
   // 2-4 slots beat 8 or more by 15%)
   c->n_slots = d.n_streams ? d.n_streams : 4;
   c->n_hp = d.n_gemm_streams ? d.n_gemm_streams : 4;
+  c->run_flags = d.run_flags;
+  c->phase_jobs = d.phase_jobs ? d.phase_jobs : 64;
   c->rel_enq.assign(cap, 0);
   c->in_free.assign(cap, 0);
   int rc = SG_ERR_CUDA;
@@ -648,9 +661,10 @@ extern "C" int sg_run_trace(sg_ctx* c, const sg_job* jobs, uint32_t n, const uin
   const uint32_t n_all = (uint32_t)c->slots.size();
   std::vector<int32_t> slot_ticket(n_all, -1);
   std::vector<uint8_t> slot_used(n_all, 0);
-  std::vector<uint32_t> pending, pend_hp;
-  pending.reserve(n);
-  pend_hp.reserve(n);
+  // admitted jobs not yet started, per kind, in grant order
+  std::vector<uint32_t> pend[3];
+  size_t pend_pos[3] = {0, 0, 0};
+  for (auto& q : pend) q.reserve(n);
   uint32_t ring_head = 0, failed = 0, bad_grants = 0;
   CK(cudaEventRecord(c->ev0, c->ctrl));
   uint32_t declared = 0;
@@ -662,9 +676,11 @@ extern "C" int sg_run_trace(sg_ctx* c, const sg_job* jobs, uint32_t n, const uin
     declared = n;
   }
   uint64_t last_progress = now_ns();
-  uint32_t last_done = 0;
-  size_t pend_pos = 0, pend_pos_hp = 0;
+  uint32_t last_done = 0, started = 0;
   uint32_t rr = 0, rr_hp = 0;
+  RunGate gate;
+  gate.apart = !(c->run_flags & SG_RUNF_OVERLAP) && !excl;
+  gate.quota = c->phase_jobs;
   while (true) {
     if (timed && declared < n) {
       uint64_t el = now_ns() - t0;
@@ -680,16 +696,36 @@ extern "C" int sg_run_trace(sg_ctx* c, const sg_job* jobs, uint32_t n, const uin
     uint32_t tail = c->h_hdr[0];
     while (ring_head < tail) {
       uint32_t t = (uint32_t)c->h_ring[(ring_head++) % c->cap];
-      (hj[t].kind == SG_KIND_GEMM && c->n_hp > 0 ? pend_hp : pending).push_back(t);
+      pend[kind_of(hj[t])].push_back(t);
     }
-    // launch granted jobs on slots whose last job has released its memory
-    // (or were never used); GEMM jobs take the high-priority slots
+    // which kinds may start now (SpMV and GEMM apart unless SG_RUNF_OVERLAP)
+    bool waiting[kKinds];
+    int64_t head_seq[kKinds];
+    uint32_t running[kKinds] = {0, 0, 0};
+    for (int k = 0; k < kKinds; k++) {
+      waiting[k] = pend_pos[k] < pend[k].size();
+      head_seq[k] = waiting[k] ? c->h_rec[pend[k][pend_pos[k]]].grant_seq : INT64_MAX;
+    }
+    if (gate.apart) {
+      for (uint32_t s = 0; s < n_all; s++) {
+        const int32_t tk = slot_ticket[s];
+        if (tk >= 0 && (uint32_t)c->h_rec[tk].status < SG_ST_DONE) running[kind_of(hj[tk])]++;
+      }
+    }
+    bool may[kKinds];
+    gate.gate(waiting, head_seq, running, may);
+    // launch admitted jobs on slots whose last job has released its memory
+    // (or were never used); GEMM jobs take the high-priority slots when
+    // there are any. Within a slot pool the earliest grant of the kinds that
+    // may start goes first.
     for (int pool = 0; pool < 2; pool++) {
-      std::vector<uint32_t>& q = pool ? pend_hp : pending;
-      size_t& pos = pool ? pend_pos_hp : pend_pos;
       const uint32_t first = pool ? c->n_slots : 0, cnt = pool ? c->n_hp : c->n_slots;
+      if (cnt == 0) continue;
       uint32_t& cursor = pool ? rr_hp : rr;
-      while (pos < q.size()) {
+      const bool serves[kKinds] = {!pool, !pool, pool == 1 || c->n_hp == 0};
+      while (true) {
+        const int kind = pick_kind(serves, may, waiting, head_seq);
+        if (kind < 0) break;
         int slot = -1;
         for (uint32_t k = 0; k < cnt; k++) {
           uint32_t s = first + (cursor + k) % cnt;
@@ -698,7 +734,11 @@ extern "C" int sg_run_trace(sg_ctx* c, const sg_job* jobs, uint32_t n, const uin
         }
         if (slot < 0) break;
         cursor = (uint32_t)slot - first + 1;
-        const uint32_t t = q[pos++];
+        const uint32_t t = pend[kind][pend_pos[kind]++];
+        started++;
+        gate.started(kind, may);
+        waiting[kind] = pend_pos[kind] < pend[kind].size();
+        head_seq[kind] = waiting[kind] ? c->h_rec[pend[kind][pend_pos[kind]]].grant_seq : INT64_MAX;
         RelHook h;
         h.eng = c->eng;
         h.ticket = t;
@@ -729,7 +769,7 @@ extern "C" int sg_run_trace(sg_ctx* c, const sg_job* jobs, uint32_t n, const uin
     if (done >= n && declared >= n) break;
     if (c->h_hdr[1]) break;
     uint64_t tn = now_ns();
-    if (done != last_done || ring_head != pend_pos + pend_pos_hp) {
+    if (done != last_done || ring_head != started) {
       last_done = done;
       last_progress = tn;
     } else if (tn - last_progress > 120ull * 1000000000ull) {

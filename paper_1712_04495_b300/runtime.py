@@ -56,13 +56,13 @@ class Scheduler:
 
     def __init__(self, pool_bytes: int, policy="first_fit", flags: int = 0, max_tickets: int = 0,
                  n_streams: int = 0, granule: int = 0, pool: torch.Tensor | None = None,
-                 n_gemm_streams: int = 0):
+                 n_gemm_streams: int = 0, run_flags: int = 0, phase_jobs: int = 0):
         _require_cuda()
         self.pool = pool if pool is not None else torch.empty(pool_bytes, dtype=torch.uint8,
                                                               device="cuda")
         self.pool_bytes = pool_bytes
         self.ctx = abi.sg_init(self.pool.data_ptr(), pool_bytes, policy, flags, max_tickets,
-                               n_streams, granule, n_gemm_streams)
+                               n_streams, granule, n_gemm_streams, run_flags, phase_jobs)
         self._tables = None
 
     # -- life cycle

@@ -52,6 +52,13 @@ def test_host_only_calls(lib):
     assert lib.sg_replay_workspace_bytes(1000) > 1000 * 48
     # argument checks happen before any device work
     assert lib.sg_init(None, None, ctypes.c_uint64(0), None) == 4
+    # an unknown start-rule flag is refused before anything is allocated
+    from paper_1712_04495_b300 import abi
+    out = ctypes.c_void_p()
+    cfg = abi.SgConfig(1, 0, 0, 0, 0, 0, 2, 0)
+    assert lib.sg_init(ctypes.byref(out), ctypes.c_void_p(1 << 20), ctypes.c_uint64(1 << 20),
+                       ctypes.byref(cfg)) == 4
+    assert out.value is None
     assert lib.sg_gemm_bf16(ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), 100, 128, 63,
                             None) == 4
 

@@ -105,12 +105,13 @@ def _check_real_log(jobs, rec, budget, policy, exclusive=False):
     invariants.check_log(j2, out, budget, policy, exclusive=exclusive, replay=False)
 
 
+@pytest.mark.parametrize("overlap", [False, True], ids=["kinds_apart", "overlap"])
 @pytest.mark.parametrize("policy", ["fifo", "first_fit"])
-def test_trace_alone_equals_mix(policy):
+def test_trace_alone_equals_mix(policy, overlap):
     abi, rt = _rt()
     budget = 48 * MIB
     tr = _small_mixed(3, 40, budget)
-    s = rt.Scheduler(budget, policy)
+    s = rt.Scheduler(budget, policy, run_flags=abi.SG_RUNF_OVERLAP if overlap else 0)
     d_jobs = rt.to_device(tr.jobs)
     d_tab = rt.device_tables(tr)
     rc, log, keep, st = s.run_trace(d_jobs, d_tab, abi.SG_RUN_SATURATED, keep=True)
@@ -249,14 +250,15 @@ def test_cancel_and_grant_notifications():
     s.shutdown()
 
 
-def test_serving_results_equal_alone_and_in_the_mix():
+@pytest.mark.parametrize("overlap", [False, True], ids=["kinds_apart", "overlap"])
+def test_serving_results_equal_alone_and_in_the_mix(overlap):
     # open-loop arrivals admitted while earlier requests run; every request's
     # output equals its output when it runs alone on the GPU
     abi, rt = _rt()
     budget = 48 * MIB
     tr = tg.trace_mixed(21, 60, 3000.0, budget, "serve_small", triad_rng=(1 << 16, 1 << 20),
                         spmv_rng=(2e3, 4e4), gemm_set=(128, 256, 512))
-    s = rt.Scheduler(budget, "first_fit")
+    s = rt.Scheduler(budget, "first_fit", run_flags=abi.SG_RUNF_OVERLAP if overlap else 0)
     d_jobs, d_tab = rt.to_device(tr.jobs), rt.device_tables(tr)
     rc, log, keep_mix, st = s.run_trace(d_jobs, d_tab, abi.SG_RUN_TIMED, keep=True)
     assert rc == abi.SG_OK
