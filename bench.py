@@ -173,6 +173,16 @@ def _threads():
         return os.cpu_count() or 1
 
 
+def workload_config(ws: int) -> dict:
+    """The workload both arms report (the same trace; the oracle arm runs a sample of it)."""
+    return {"workload": WORKLOAD + "_t0", "jobs": 256, "pool_gib": 16, "policy": "first_fit",
+            "arrivals": "t=0 (saturated)", "seed": 0,
+            "start_rule": "SpMV and GEMM jobs in alternating phases (<= 64 starts), "
+                          "triads beside either; stream slots 4 + 4 GEMM",
+            "l2": "inputs larger than L2 (about 50 GB of job data per step)",
+            "parallelism": f"replicas x{ws}"}
+
+
 def reference_arm(args):
     ws, rank, _ = _dist_env()
     if rank != 0:
@@ -192,8 +202,7 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "jobs/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "policy": "first_fit",
-                                            "arrivals": "t=0 (saturated)"},
+            "data": "synthetic", "config": workload_config(ws),
             "cpu_baseline": {"value": v, "unit": "jobs/s", "cores": _threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": "jobs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -791,6 +800,7 @@ def main():
 
     trace = tg.trace_c2(saturated=True)
     n = len(trace)
+    assert n == workload_config(1)["jobs"]
     sched = runtime.Scheduler(trace.budget, "first_fit")
     d_jobs = runtime.to_device(trace.jobs)
     d_tab = runtime.device_tables(trace)
@@ -899,12 +909,7 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "int64 admission; f32 triad/spmv; bf16 in, f32 acc gemm",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD + "_t0", "jobs": n, "pool_gib": 16, "policy": "first_fit",
-                           "arrivals": "t=0 (saturated)", "seed": 0,
-                           "start_rule": "SpMV and GEMM jobs in alternating phases (<= 64 starts), "
-                                         "triads beside either; stream slots 4 + 4 GEMM",
-                           "l2": "inputs larger than L2 (about 50 GB of job data per step)",
-                           "parallelism": f"replicas x{ws}"},
+                "config": workload_config(ws),
                 "gpu_launches": launches, "clocks": clocks, "wall_s": wall,
                 "autotune_gemm_tile": {str(sh[0]): abi.gemm_tile_name(w) for sh, w, _ in tuned}}
         line.update(extra)
