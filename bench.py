@@ -178,7 +178,8 @@ def workload_config(ws: int) -> dict:
     return {"workload": WORKLOAD + "_t0", "jobs": 256, "pool_gib": 16, "policy": "first_fit",
             "arrivals": "t=0 (saturated)", "seed": 0,
             "start_rule": "SpMV and GEMM jobs in alternating phases (<= 64 starts), "
-                          "triads beside either; stream slots 4 + 4 GEMM",
+                          "triads beside either; jobs declared >= 1 ms one at a time; "
+                          "stream slots 4 + 4 GEMM",
             "l2": "inputs larger than L2 (about 50 GB of job data per step)",
             "parallelism": f"replicas x{ws}"}
 
@@ -403,6 +404,62 @@ def serving_section(torch, abi, runtime, requests: int, rates=(1000, 2000, 5000,
                 "makespan_ms": st["makespan_ns"] / 1e6, "peak_used_gib": st["peak_used"] / 2 ** 30}
         s.shutdown()
     del pool
+    torch.cuda.empty_cache()
+    return out
+
+
+def _run_summary(st: dict, n: int) -> dict:
+    return {"makespan_ms": st["makespan_ns"] / 1e6, "jobs_per_s": n / (st["makespan_ns"] * 1e-9),
+            "wait_p50_ms": st["wait_p50_ns"] / 1e6, "wait_p99_ms": st["wait_p99_ns"] / 1e6,
+            "turnaround_p99_ms": st["turnaround_p99_ns"] / 1e6, "peak_used_gib": st["peak_used"] / 2 ** 30,
+            "frag_waits": st["frag_waits"]}
+
+
+def configs_section(torch, abi, runtime) -> dict:
+    """The two other admission workloads, co-scheduled against exclusive-serial
+    (one run each): 8 triads at t=0 in a 1 GiB pool under FIFO, and memory
+    pressure -- 128 jobs of 2-60 GiB in a 170 GiB pool arriving in bursts of
+    16 every 200 ms, first fit, where waiters are woken by releases."""
+    out = {}
+    tr = tg.trace_c1()
+    s = runtime.Scheduler(tr.budget, "fifo")
+    d_jobs, d_tab = runtime.to_device(tr.jobs), runtime.device_tables(tr)
+    row = {"workload": tr.name, "jobs": len(tr), "policy": "fifo"}
+    for name, mode in (("co_scheduled", abi.SG_RUN_SATURATED),
+                       ("exclusive_serial", abi.SG_RUN_SATURATED | abi.SG_RUN_EXCLUSIVE)):
+        runs = []
+        for _ in range(5):
+            rc, _, _, st = s.run_trace(d_jobs, d_tab, mode)
+            assert rc == abi.SG_OK, st
+            runs.append(st)
+        row[name] = _run_summary(sorted(runs, key=lambda r: r["makespan_ns"])[2], len(tr))
+    row["makespan_ratio"] = row["co_scheduled"]["makespan_ms"] / row["exclusive_serial"]["makespan_ms"]
+    out["triad8"] = row
+    s.shutdown()
+    del s
+    tr = tg.trace_c3()
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    if free < tr.budget + (8 << 30):
+        out["pressure"] = {"workload": tr.name, "skipped": f"needs {tr.budget >> 30} GiB free"}
+        return out
+    s = runtime.Scheduler(tr.budget, "first_fit")
+    d_jobs, d_tab = runtime.to_device(tr.jobs), runtime.device_tables(tr)
+    row = {"workload": tr.name, "jobs": len(tr), "policy": "first_fit",
+           "need_gib": [round(float(tr.jobs["need"].min()) / 2 ** 30, 1),
+                        round(float(tr.jobs["need"].max()) / 2 ** 30, 1)]}
+    for name, mode in (("co_scheduled", abi.SG_RUN_TIMED),
+                       ("exclusive_serial", abi.SG_RUN_TIMED | abi.SG_RUN_EXCLUSIVE),
+                       ("co_scheduled_t0", abi.SG_RUN_SATURATED),
+                       ("exclusive_serial_t0", abi.SG_RUN_SATURATED | abi.SG_RUN_EXCLUSIVE)):
+        rc, _, _, st = s.run_trace(d_jobs, d_tab, mode)
+        assert rc == abi.SG_OK, st
+        row[name] = _run_summary(st, len(tr))
+    row["makespan_ratio"] = row["co_scheduled"]["makespan_ms"] / row["exclusive_serial"]["makespan_ms"]
+    row["makespan_ratio_t0"] = row["co_scheduled_t0"]["makespan_ms"] / row["exclusive_serial_t0"]["makespan_ms"]
+    out["pressure"] = row
+    s.shutdown()
+    del s, d_jobs, d_tab
     torch.cuda.empty_cache()
     return out
 
@@ -891,6 +948,7 @@ def main():
             extra["mixed_plan_graph"] = mixed_plan_section(torch, abi, runtime)
             extra["batching"] = batching_section(torch, abi, runtime)
             extra["serving"] = serving_section(torch, abi, runtime, args.serving_requests)
+            extra["configs"] = configs_section(torch, abi, runtime)
         kr = kernel_roofline(torch, abi, peaks)
         extra["kernels"] = kr
         extra["roofline"] = {k: kr["gemm"][k] for k in ("bound", "achieved", "peak", "unit", "frac",

@@ -76,7 +76,7 @@ extern "C" {
 typedef struct sg_job {
     uint64_t arrival_ns;   /* arrival time on the trace clock              */
     uint64_t need;         /* declared bytes (rounded up to the granule)   */
-    uint64_t duration_ns;  /* declared duration: the replay clock only     */
+    uint64_t duration_ns;  /* declared duration: the replay clock; the runner treats >= 1 ms as a long job */
     uint64_t timeout_ns;   /* UINT64_MAX = wait forever; 0 = non-blocking  */
     uint64_t key;          /* SplitMix64 key of the job's data             */
     uint64_t p0;           /* triad n | spmv rows | gemm M                 */
@@ -119,7 +119,11 @@ typedef struct sg_config {
  * starts, which in a real run moves its release and so later grants. On B300 an SpMV's random gathers and a GEMM's operand stream
  * both load L2; on the mixed trace, running the two kinds in turn finishes
  * sooner and with a shorter tail turnaround under load than overlapping
- * them. SG_RUNF_OVERLAP starts every admitted job as soon as a slot frees. */
+ * them. Jobs declared to run 1 ms or longer (sg_job.duration_ns) also run
+ * one at a time, with shorter jobs beside them: each fills the GPU on its
+ * own, and two together finish later than one after the other.
+ * SG_RUNF_OVERLAP turns both rules off and starts every admitted job as soon
+ * as a slot frees. */
 #define SG_RUNF_OVERLAP  1u
 
 typedef struct sg_grant {

@@ -680,7 +680,10 @@ extern "C" int sg_run_trace(sg_ctx* c, const sg_job* jobs, uint32_t n, const uin
   uint32_t rr = 0, rr_hp = 0;
   RunGate gate;
   gate.apart = !(c->run_flags & SG_RUNF_OVERLAP) && !excl;
+  gate.one_long = gate.apart;
   gate.quota = c->phase_jobs;
+  std::vector<uint8_t> is_long(n, 0);
+  for (uint32_t j = 0; j < n; j++) is_long[j] = hj[j].duration_ns >= kLongJobNs;
   while (true) {
     if (timed && declared < n) {
       uint64_t el = now_ns() - t0;
@@ -701,7 +704,7 @@ extern "C" int sg_run_trace(sg_ctx* c, const sg_job* jobs, uint32_t n, const uin
     // which kinds may start now (SpMV and GEMM apart unless SG_RUNF_OVERLAP)
     bool waiting[kKinds];
     int64_t head_seq[kKinds];
-    uint32_t running[kKinds] = {0, 0, 0};
+    uint32_t running[kKinds] = {0, 0, 0}, long_running = 0;
     for (int k = 0; k < kKinds; k++) {
       waiting[k] = pend_pos[k] < pend[k].size();
       head_seq[k] = waiting[k] ? c->h_rec[pend[k][pend_pos[k]]].grant_seq : INT64_MAX;
@@ -709,7 +712,10 @@ extern "C" int sg_run_trace(sg_ctx* c, const sg_job* jobs, uint32_t n, const uin
     if (gate.apart) {
       for (uint32_t s = 0; s < n_all; s++) {
         const int32_t tk = slot_ticket[s];
-        if (tk >= 0 && (uint32_t)c->h_rec[tk].status < SG_ST_DONE) running[kind_of(hj[tk])]++;
+        if (tk >= 0 && (uint32_t)c->h_rec[tk].status < SG_ST_DONE) {
+          running[kind_of(hj[tk])]++;
+          long_running += is_long[tk];
+        }
       }
     }
     bool may[kKinds];
@@ -726,6 +732,10 @@ extern "C" int sg_run_trace(sg_ctx* c, const sg_job* jobs, uint32_t n, const uin
       while (true) {
         const int kind = pick_kind(serves, may, waiting, head_seq);
         if (kind < 0) break;
+        if (!gate.may_start(is_long[pend[kind][pend_pos[kind]]], long_running)) {
+          may[kind] = false;   // this kind's next job waits for the long job running
+          continue;
+        }
         int slot = -1;
         for (uint32_t k = 0; k < cnt; k++) {
           uint32_t s = first + (cursor + k) % cnt;
@@ -737,6 +747,7 @@ extern "C" int sg_run_trace(sg_ctx* c, const sg_job* jobs, uint32_t n, const uin
         const uint32_t t = pend[kind][pend_pos[kind]++];
         started++;
         gate.started(kind, may);
+        long_running += is_long[t];
         waiting[kind] = pend_pos[kind] < pend[kind].size();
         head_seq[kind] = waiting[kind] ? c->h_rec[pend[kind][pend_pos[kind]]].grant_seq : INT64_MAX;
         RelHook h;

@@ -7,7 +7,10 @@
 // an SpMV's random gathers and a GEMM's operand stream both load L2, and
 // running them in turn finishes the mixed trace sooner, with shorter tail
 // turnaround under load, than overlapping them. SG_RUNF_OVERLAP turns the
-// rule off. Host code only, no CUDA dependency (tested on the CPU).
+// rule off. Long jobs (declared duration of 1 ms or more) run one at a time,
+// with short jobs beside them: on B300 each fills the GPU alone, and two of
+// them together finish later than one after the other. Host code only, no
+// CUDA dependency (tested on the CPU).
 #pragma once
 #include <stdint.h>
 
@@ -15,8 +18,13 @@ namespace sg {
 
 enum : int { kKindTriad = 0, kKindSpmv = 1, kKindGemm = 2, kKinds = 3 };
 
+// A job declared to run this long fills the GPU on its own for long enough
+// that company only slows it (launch gaps are a few percent of it at most).
+constexpr uint64_t kLongJobNs = 1000000;
+
 struct RunGate {
   bool apart = true;        // keep SpMV and GEMM jobs apart
+  bool one_long = true;     // at most one long job runs at a time
   uint32_t quota = 64;      // starts of one kind per phase while the other kind waits
   int phase = -1;           // kKindSpmv or kKindGemm; -1 before the first phase
   uint32_t phase_started = 0;
@@ -50,6 +58,10 @@ struct RunGate {
     may[kKindGemm] = phase == kKindGemm && running[kKindSpmv] == 0;
     other_waits = phase >= 0 && waiting[phase == kKindSpmv ? kKindGemm : kKindSpmv];
   }
+
+  // May a job start while long_running long jobs run? `is_long`: its
+  // declared duration is at least kLongJobNs.
+  bool may_start(bool is_long, uint32_t long_running) const { return !one_long || !is_long || long_running == 0; }
 
   // A job of `kind` was started: count it against the phase and keep the
   // other kind from starting beside it.

@@ -26,18 +26,20 @@ uint64_t next(uint64_t* s) {   // SplitMix64
 // starts of one kind in one phase while the other kind waited
 extern "C" int ph_sim(uint64_t seed, int n_jobs, int n_other, int n_gemm, int apart, int quota, int64_t* stats) {
   uint64_t rng = seed;
-  std::vector<int> kind(n_jobs), dur(n_jobs), admit(n_jobs);
+  std::vector<int> kind(n_jobs), dur(n_jobs), admit(n_jobs), is_long(n_jobs);
   int t_admit = 0;
   for (int j = 0; j < n_jobs; j++) {            // admitted in index order (grant order)
     const uint64_t r = next(&rng) % 10;
     kind[j] = r < 4 ? kKindTriad : r < 7 ? kKindSpmv : kKindGemm;
     dur[j] = 1 + (int)(next(&rng) % 40);
+    is_long[j] = next(&rng) % 5 == 0;   // a long job (declared duration of at least kLongJobNs)
     t_admit += (int)(next(&rng) % 3);
     admit[j] = t_admit;
   }
   RunGate gate;
   gate.apart = apart != 0;
   gate.quota = (uint32_t)quota;
+  gate.one_long = apart != 0;
   const int n_all = n_other + n_gemm;
   std::vector<int> slot_job(n_all, -1), end_t(n_all, 0);
   std::vector<int> pend[kKinds];
@@ -55,12 +57,13 @@ extern "C" int ph_sim(uint64_t seed, int n_jobs, int n_other, int n_gemm, int ap
     while (admitted < n_jobs && admit[admitted] <= t) { pend[kind[admitted]].push_back(admitted); admitted++; }
     bool waiting[kKinds];
     int64_t head[kKinds];
-    uint32_t running[kKinds] = {0, 0, 0};
+    uint32_t running[kKinds] = {0, 0, 0}, long_running = 0;
     for (int k = 0; k < kKinds; k++) {
       waiting[k] = pos[k] < pend[k].size();
       head[k] = waiting[k] ? pend[k][pos[k]] : INT64_MAX;
     }
-    for (int s = 0; s < n_all; s++) if (slot_job[s] >= 0) running[kind[slot_job[s]]]++;
+    for (int s = 0; s < n_all; s++)
+      if (slot_job[s] >= 0) { running[kind[slot_job[s]]]++; long_running += is_long[slot_job[s]]; }
     bool may[kKinds];
     gate.gate(waiting, head, running, may);
     if (gate.apart && gate.phase != last_phase) { phases++; last_phase = gate.phase; run_in_phase = 0; }
@@ -71,6 +74,10 @@ extern "C" int ph_sim(uint64_t seed, int n_jobs, int n_other, int n_gemm, int ap
       while (true) {
         const int k = pick_kind(serves, may, waiting, head);
         if (k < 0) break;
+        if (!gate.may_start(is_long[pend[k][pos[k]]], long_running)) {
+          may[k] = false;
+          continue;
+        }
         int slot = -1;
         for (int s = first; s < first + cnt; s++) if (slot_job[s] < 0) { slot = s; break; }
         if (slot < 0) break;
@@ -85,6 +92,9 @@ extern "C" int ph_sim(uint64_t seed, int n_jobs, int n_other, int n_gemm, int ap
         end_t[slot] = t + dur[j];
         started_at[j] = t;
         running[k]++;
+        long_running += is_long[j];
+        // property 7: two long jobs never run at the same time
+        if (gate.one_long && long_running > 1) return 7;
         if (gate.apart && (k == kKindSpmv || k == kKindGemm)) {
           const int other = k == kKindSpmv ? kKindGemm : kKindSpmv;
           // property 2: SpMV and GEMM never run at the same time

@@ -1,6 +1,7 @@
 """The trace runner's start rule (csrc/phases.h), on the CPU: SpMV and GEMM
 jobs are kept apart in alternating phases, triads run beside either, a
-phase yields after its quota while the other kind waits, nothing starves,
+phase yields after its quota while the other kind waits, no two long jobs
+(declared duration of 1 ms or more) run at once, nothing starves,
 and each slot pool starts the earliest-admitted job it may start. The rule
 is driven by a discrete simulation of admitted jobs on stream slots
 (tests/phases_harness), which mirrors sg_run_trace's loop."""
@@ -19,7 +20,8 @@ _ERRORS = {1: "pick is not the earliest admitted job the pool may start",
            3: "a free slot stayed free while a job it serves could start",
            4: "without the rule a kind was held back",
            5: "a job started before it was admitted",
-           6: "a job never started"}
+           6: "a job never started",
+           7: "two long jobs ran at the same time"}
 
 
 @pytest.fixture(scope="module")
