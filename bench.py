@@ -938,6 +938,9 @@ def main():
         sched.shutdown()
         del sched
         torch.cuda.empty_cache()
+        # the job kernels timed alone, before the long extra sections heat the GPU
+        kr = kernel_roofline(torch, abi, peaks)
+        extra["kernels"] = kr
         if not args.no_extras:
             extra["lifecycle"] = lifecycle_section(torch, abi, runtime)
             extra["client_server"] = client_server_section(torch, abi, runtime)
@@ -949,8 +952,6 @@ def main():
             extra["batching"] = batching_section(torch, abi, runtime)
             extra["serving"] = serving_section(torch, abi, runtime, args.serving_requests)
             extra["configs"] = configs_section(torch, abi, runtime)
-        kr = kernel_roofline(torch, abi, peaks)
-        extra["kernels"] = kr
         extra["roofline"] = {k: kr["gemm"][k] for k in ("bound", "achieved", "peak", "unit", "frac",
                                                         "traffic")}
         extra["roofline"]["kernel"] = kr["gemm"]["kernel"]
