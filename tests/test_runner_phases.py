@@ -13,7 +13,7 @@ import tempfile
 import pytest
 
 sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "phases_harness"))
-import build as phases_build  # noqa: E402
+import phases_build  # noqa: E402
 
 _ERRORS = {1: "pick is not the earliest admitted job the pool may start",
            2: "an SpMV and a GEMM ran at the same time",
