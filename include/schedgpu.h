@@ -221,8 +221,9 @@ int sg_launch(sg_ctx* ctx, sg_ticket t, const sg_job* job, const uint64_t* table
               void* stream);
 
 /* Run a whole trace: declare every job (at t=0 or at its arrival time),
- * launch each as it is granted on a free stream slot, until every job is
- * released. Ticket i is job i. jobs/log: device buffers (host buffers with
+ * launch each as it is granted on a free stream slot, under the start rules
+ * of sg_config.run_flags (SpMV and GEMM in turn, long jobs one at a time),
+ * until every job is released. Ticket i is job i. jobs/log: device buffers (host buffers with
  * SG_RUN_HOST_IO, copied in and out inside the call). log receives one
  * sg_record per job (device clock). keep (SG_RUN_KEEP): n uint64 output
  * digests (see sg_digest), else NULL. stats may be NULL. */
