@@ -952,10 +952,14 @@ def main():
             extra["batching"] = batching_section(torch, abi, runtime)
             extra["serving"] = serving_section(torch, abi, runtime, args.serving_requests)
             extra["configs"] = configs_section(torch, abi, runtime)
-        extra["roofline"] = {k: kr["gemm"][k] for k in ("bound", "achieved", "peak", "unit", "frac",
+        # the kernel with the largest share of a step's launch list is the CSR
+        # SpMV (profiles/launches_mixed256_16GiB_t0.md), just ahead of the GEMM
+        extra["roofline"] = {k: kr["spmv"][k] for k in ("bound", "achieved", "peak", "unit", "frac",
                                                         "traffic")}
-        extra["roofline"]["kernel"] = kr["gemm"]["kernel"]
-        extra["roofline"]["peak_source"] = peaks["source"] + " (burst, kernel timed alone)"
+        extra["roofline"]["kernel"] = kr["spmv"]["kernel"]
+        extra["roofline"]["peak_source"] = peaks["source"] + " (copy bandwidth, kernel timed alone)"
+        extra["roofline"]["note"] = ("bound by random x gathers (L1/L2 sector rate), not by HBM: HBM traffic "
+                                     "equals the algorithmic bytes; kernels.gemm has the tcgen05 GEMM")
         if not args.no_cpu_baseline:
             d, e = oracle_sample(trace, 20.0)
             extra["cpu_baseline"] = {"value": d / e, "unit": "jobs/s", "cores": _threads(),
