@@ -221,3 +221,28 @@ def test_autotuner_picks_a_width_and_gemm_stays_exact():
     finally:
         abi.sg_autotune_clear()
     assert abi.sg_gemm_tile(256, 256) == abi.gemm_tile(128, 64)
+
+
+def test_empty_inputs_are_no_ops():
+    # zero-sized jobs return SG_OK and write nothing; an empty trace runs no job
+    abi = _abi()
+    from paper_1712_04495_b300 import runtime
+    sentinel = torch.full((64,), 7.0, dtype=torch.float32, device="cuda")
+    p = sentinel.data_ptr()
+    assert abi.sg_triad(p, p, p, 3.0, 0) == abi.SG_OK
+    assert abi.sg_gen_triad(p, p, 0, 1) == abi.SG_OK
+    rp = torch.zeros(4, dtype=torch.int32, device="cuda")
+    assert abi.sg_spmv(rp.data_ptr(), False, p, p, p, p, 0) == abi.SG_OK
+    bf = torch.zeros(64, dtype=torch.int16, device="cuda")
+    assert abi.sg_gemm_bf16(bf.data_ptr(), bf.data_ptr(), p, 0, 128, 64) == abi.SG_OK
+    assert abi.sg_gemm_bf16(bf.data_ptr(), bf.data_ptr(), p, 128, 0, 64) == abi.SG_OK
+    out = torch.full((1,), 5, dtype=torch.int64, device="cuda")
+    assert abi.sg_digest(p, 0, out.data_ptr()) == abi.SG_OK
+    torch.cuda.synchronize()
+    assert torch.all(sentinel == 7.0) and int(out.item()) == 5
+    s = runtime.Scheduler(1 << 20, "first_fit")
+    rc, st = abi.sg_run_trace(s.ctx, 0, 0, 0, abi.SG_RUN_SATURATED, 0)
+    assert rc == abi.SG_OK and st["jobs_done"] == 0 and st["makespan_ns"] == 0
+    eng = abi.sg_state(s.ctx)
+    assert eng["used"] == 0 and eng["waiting"] == 0 and eng["error_flags"] == 0
+    s.shutdown()
