@@ -152,8 +152,10 @@ static int try_grant(sim_t* s, int j, uint64_t t) {
     s->out[j].grant_seq = s->seq++;
     s->out[j].grant_t = t;
     s->out[j].offset = off;
-    ev_t e = { t + s->duration[j], EV_COMPLETE, j };
-    heap_push(&s->ev, e);
+    if (s->duration) {                                 /* trace mode: completion at grant + duration */
+        ev_t e = { t + s->duration[j], EV_COMPLETE, j };
+        heap_push(&s->ev, e);
+    }
     return 1;
 }
 
@@ -285,5 +287,157 @@ int des_run(int n, const uint64_t* arrival, const uint64_t* need, const uint64_t
     }
     st->makespan = (first == UINT64_MAX) ? 0 : last - first;
     free(s.need_g); free(s.q); free(s.ext.off); free(s.ext.len); free(s.ev.v);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Op-sequence mode: the life-cycle calls of Sec. IV issued one at a time by
+ * clients, instead of a trace whose completions follow declared durations.
+ *
+ *   DECLARE(need, prio)  pre-allocation (preCudaMalloc): a request larger
+ *                        than the pool is refused at once and gets no
+ *                        ticket; otherwise the next ticket number is handed
+ *                        out, the request joins the queue (or, under
+ *                        FLAG_FIFO_BYPASS and FIFO, is served at once if it
+ *                        fits) and the policy pass runs.
+ *   RELEASE(ticket, b)   post-free (postCudaFree) of b declared bytes. b = 0,
+ *                        or b at least the bytes the ticket still holds,
+ *                        frees all of it and ends the ticket. A smaller b
+ *                        shrinks the grant: the ticket keeps the first
+ *                        (held - b) bytes, rounded up to the granule, at the
+ *                        front of its extent, and the rest goes back to the
+ *                        free list. The notification pass runs either way.
+ *                        A ticket that holds nothing is refused (RC_INVALID),
+ *                        and so is a second release after a full one.
+ *   CANCEL(ticket)       the expiry of a blocking wait: a waiting ticket
+ *                        leaves the queue (RC_TIMEOUT) and the pass re-runs;
+ *                        a granted one reports RC_OK, a withdrawn one
+ *                        RC_TIMEOUT again, a finished one RC_INVALID.
+ *
+ * After every op the scalar state is recorded (used and peak bytes, grants,
+ * passes, fragmentation-blocked passes, the free extents and the largest,
+ * waiting and finished tickets), so a run can be compared step by step.
+ */
+enum { OP_DECLARE = 0, OP_RELEASE = 1, OP_CANCEL = 2 };
+enum { RC_OK = 0, RC_NOT_READY = 1, RC_TIMEOUT = 2, RC_TOO_LARGE = 3, RC_INVALID = 4 };
+
+typedef struct {
+    uint64_t t;              /* logical time of the call */
+    int32_t type;            /* OP_* */
+    int32_t ticket;          /* RELEASE / CANCEL: the ticket */
+    uint64_t arg;            /* DECLARE: need in bytes; RELEASE: bytes freed (0 = all) */
+    int32_t prio;            /* DECLARE: priority (smaller = higher) */
+    int32_t pad;
+} des_op;
+
+typedef struct {
+    int32_t rc;              /* RC_* */
+    int32_t ticket;          /* DECLARE: ticket handed out, -1 if refused */
+    uint64_t used, peak_used, grants, passes, frag_waits, max_free_extent;
+    uint32_t free_extents, waiting, done, pad;
+} des_op_out;
+
+/* outcome of a single op on the simulator state (see the comment above) */
+static int32_t op_step(sim_t* s, const des_op* op, int* n_tickets, uint64_t* raw, int32_t* prio,
+                       int32_t* ticket_out) {
+    *ticket_out = -1;
+    if (op->type == OP_DECLARE) {
+        uint64_t g = (op->arg + s->granule - 1) / s->granule * s->granule;
+        if (g == 0) g = s->granule;
+        if (g > s->budget) return RC_TOO_LARGE;
+        int j = (*n_tickets)++;
+        *ticket_out = j;
+        s->need_g[j] = g;
+        raw[j] = op->arg;
+        prio[j] = op->prio;
+        s->out[j].status = ST_PENDING;
+        s->out[j].grant_seq = -1;
+        if ((s->flags & FLAG_FIFO_BYPASS) && s->policy == POL_FIFO && try_grant(s, j, op->t))
+            return RC_OK;
+        q_insert(s, j);
+        policy_pass(s, op->t);
+        return RC_OK;
+    }
+    int j = op->ticket;
+    if (j < 0 || j >= *n_tickets) return RC_INVALID;
+    if (op->type == OP_RELEASE) {
+        if (s->out[j].status != ST_RUNNING) return RC_INVALID;
+        if (op->arg == 0 || op->arg >= raw[j]) {
+            ext_free(&s->ext, s->out[j].offset, s->need_g[j]);
+            s->used -= s->need_g[j];
+            s->out[j].status = ST_DONE;
+            s->out[j].done_t = op->t;
+        } else {
+            uint64_t keep_raw = raw[j] - op->arg;
+            uint64_t keep = (keep_raw + s->granule - 1) / s->granule * s->granule;
+            uint64_t freed = s->need_g[j] - keep;
+            if (freed > 0) ext_free(&s->ext, s->out[j].offset + keep, freed);
+            s->used -= freed;
+            s->need_g[j] = keep;
+            raw[j] = keep_raw;
+        }
+        policy_pass(s, op->t);
+        return RC_OK;
+    }
+    if (op->type == OP_CANCEL) {
+        int32_t st = s->out[j].status;
+        if (st == ST_RUNNING) return RC_OK;
+        if (st == ST_TIMEOUT) return RC_TIMEOUT;
+        if (st != ST_QUEUED) return RC_INVALID;
+        for (int i = 0; i < s->qn; i++) if (s->q[i] == j) { q_remove_at(s, i); break; }
+        s->out[j].status = ST_TIMEOUT;
+        s->out[j].done_t = op->t;
+        policy_pass(s, op->t);
+        return RC_TIMEOUT;
+    }
+    return RC_INVALID;
+}
+
+/* Run n_ops life-cycle calls; tickets[] gets one record per ticket handed out
+ * (at most n_ops), ops_out[] one state record per op; *n_tickets_out the
+ * number of tickets. Returns 0, or a negative value on bad arguments. */
+int des_ops_run(int n_ops, const des_op* ops, uint64_t budget, uint64_t granule, int policy, int flags,
+                des_out* tickets, des_op_out* ops_out, int* n_tickets_out) {
+    if (n_ops < 0 || granule == 0 || policy < 0 || policy > 3) return -1;
+    sim_t s;
+    des_stats st;
+    memset(&s, 0, sizeof s);
+    memset(&st, 0, sizeof st);
+    int cap = n_ops + 1;
+    s.granule = granule; s.policy = policy; s.flags = flags; s.out = tickets; s.st = &st;
+    s.budget = budget / granule * granule;
+    s.duration = NULL;
+    uint64_t* raw = (uint64_t*)malloc(sizeof(uint64_t) * cap);
+    int32_t* prio = (int32_t*)malloc(sizeof(int32_t) * cap);
+    s.prio = prio;
+    s.need_g = (uint64_t*)malloc(sizeof(uint64_t) * cap);
+    s.q = (int*)malloc(sizeof(int) * cap);
+    s.ext.off = (uint64_t*)malloc(sizeof(uint64_t) * (cap + 2));
+    s.ext.len = (uint64_t*)malloc(sizeof(uint64_t) * (cap + 2));
+    if (!raw || !prio || !s.need_g || !s.q || !s.ext.off || !s.ext.len) return -2;
+    if (s.budget > 0) { s.ext.off[0] = 0; s.ext.len[0] = s.budget; s.ext.n = 1; }
+    for (int j = 0; j < n_ops; j++) {
+        tickets[j].status = ST_PENDING; tickets[j].pad = 0; tickets[j].grant_seq = -1;
+        tickets[j].grant_t = 0; tickets[j].offset = 0; tickets[j].done_t = 0;
+    }
+    int n_tickets = 0;
+    for (int k = 0; k < n_ops; k++) {
+        des_op_out* o = &ops_out[k];
+        memset(o, 0, sizeof *o);
+        o->rc = op_step(&s, &ops[k], &n_tickets, raw, prio, &o->ticket);
+        o->used = s.used;
+        o->peak_used = st.peak_used;
+        o->grants = (uint64_t)s.seq;
+        o->passes = st.passes;
+        o->frag_waits = st.frag_waits;
+        o->free_extents = (uint32_t)s.ext.n;
+        for (int i = 0; i < s.ext.n; i++)
+            if (s.ext.len[i] > o->max_free_extent) o->max_free_extent = s.ext.len[i];
+        o->waiting = (uint32_t)s.qn;
+        for (int j = 0; j < n_tickets; j++)
+            if (tickets[j].status == ST_DONE || tickets[j].status == ST_TIMEOUT) o->done++;
+    }
+    *n_tickets_out = n_tickets;
+    free(raw); free(prio); free(s.need_g); free(s.q); free(s.ext.off); free(s.ext.len);
     return 0;
 }

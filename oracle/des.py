@@ -1,4 +1,5 @@
-"""ctypes front of the C discrete-event simulator (``des.c``)."""
+"""ctypes front of the C discrete-event simulator (``des.c``): whole traces
+(``simulate``) and sequences of life-cycle calls (``simulate_ops``)."""
 from __future__ import annotations
 
 import ctypes
@@ -34,6 +35,9 @@ def _load():
         lib.des_run.argtypes = [ctypes.c_int, P, P, P, P, P, ctypes.c_uint64, ctypes.c_uint64,
                                 ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(_Stats)]
         lib.des_run.restype = ctypes.c_int
+        lib.des_ops_run.argtypes = [ctypes.c_int, P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                    ctypes.c_int, P, P, ctypes.POINTER(ctypes.c_int)]
+        lib.des_ops_run.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -68,3 +72,64 @@ def simulate(jobs: np.ndarray, budget: int, policy, granule: int = 256, flags: i
         raise RuntimeError(f"des_run failed: {rc}")
     return out, {"peak_used": st.peak_used, "frag_waits": st.frag_waits, "passes": st.passes,
                  "makespan": st.makespan}
+
+
+# ---------------------------------------------------------------- op mode
+OP_DECLARE, OP_RELEASE, OP_CANCEL = range(3)
+RC_OK, RC_NOT_READY, RC_TIMEOUT, RC_TOO_LARGE, RC_INVALID = range(5)
+
+OP_DTYPE = np.dtype([("t", "<u8"), ("type", "<i4"), ("ticket", "<i4"), ("arg", "<u8"), ("prio", "<i4"),
+                     ("pad", "<i4")])
+OP_OUT_DTYPE = np.dtype([("rc", "<i4"), ("ticket", "<i4"), ("used", "<u8"), ("peak_used", "<u8"),
+                         ("grants", "<u8"), ("passes", "<u8"), ("frag_waits", "<u8"),
+                         ("max_free_extent", "<u8"), ("free_extents", "<u4"), ("waiting", "<u4"),
+                         ("done", "<u4"), ("pad2", "<u4")])
+
+
+def make_ops(items) -> np.ndarray:
+    """Op records from tuples: ("declare", need[, prio]), ("release", ticket[, bytes]),
+    ("cancel", ticket); logical time = position in the list."""
+    ops = np.zeros(len(items), dtype=OP_DTYPE)
+    for k, it in enumerate(items):
+        ops["t"][k] = k
+        kind = it[0]
+        if kind == "declare":
+            ops["type"][k] = OP_DECLARE
+            ops["arg"][k] = it[1]
+            ops["prio"][k] = it[2] if len(it) > 2 else 0
+            ops["ticket"][k] = -1
+        elif kind == "release":
+            ops["type"][k] = OP_RELEASE
+            ops["ticket"][k] = it[1]
+            ops["arg"][k] = it[2] if len(it) > 2 else 0
+        elif kind == "cancel":
+            ops["type"][k] = OP_CANCEL
+            ops["ticket"][k] = it[1]
+        else:
+            raise ValueError(kind)
+    return ops
+
+
+def simulate_ops(ops: np.ndarray, budget: int, policy, granule: int = 256, flags: int = 0):
+    """Run a sequence of life-cycle calls (``OP_DTYPE`` records, or tuples for
+    ``make_ops``) through the op-sequence mode of the simulator.
+
+    Returns ``(tickets, per_op)``: one ``OUT_DTYPE`` record per ticket handed
+    out (status, grant_seq, grant_t, offset, done_t) and one ``OP_OUT_DTYPE``
+    record per op (its result code, the ticket a declare got, and the scalar
+    state after the op).
+    """
+    if not isinstance(ops, np.ndarray):
+        ops = make_ops(ops)
+    ops = np.ascontiguousarray(ops, dtype=OP_DTYPE)
+    pol = POLICIES[policy] if isinstance(policy, str) else int(policy)
+    n = len(ops)
+    tickets = np.zeros(max(n, 1), dtype=OUT_DTYPE)
+    per_op = np.zeros(max(n, 1), dtype=OP_OUT_DTYPE)
+    nt = ctypes.c_int(0)
+    lib = _load()
+    rc = lib.des_ops_run(n, _ptr(ops), int(budget), int(granule), pol, int(flags), _ptr(tickets),
+                         _ptr(per_op), ctypes.byref(nt))
+    if rc != 0:
+        raise RuntimeError(f"des_ops_run failed: {rc}")
+    return tickets[: nt.value].copy(), per_op[:n].copy()

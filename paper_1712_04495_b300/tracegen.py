@@ -445,3 +445,50 @@ def random_admission_trace(seed: int, n_jobs: int, budget: int, max_arrival: int
     jobs["timeout_ns"] = tmo
     jobs["kind"] = KIND_TRIAD
     return jobs
+
+
+def random_lifecycle_calls(seed: int, n_ops: int, budget: int, prio_levels: int = 1,
+                           p_declare: float = 0.45, p_release: float = 0.35) -> list:
+    """A seeded sequence of life-cycle calls by many clients, for step-by-step
+    tests of a live scheduler: ("declare", need, prio), ("release", ticket,
+    bytes) and ("cancel", ticket). Tickets are numbered in declare order.
+
+    Needs are log-uniform between 1 byte and half the pool, with a few of 0
+    bytes and a few of the whole pool; none is larger than the pool, so every
+    declare gets a ticket. A release or cancel names a ticket declared
+    earlier, whatever its state (the scheduler refuses what is not valid).
+    Release sizes: 0 (all), a part of the declared need, or more than it.
+    """
+    key = int(sm64_at(seed ^ 0x11FE, 0))
+    idx = np.arange(n_ops)
+    u = [_u01(key, 6 * idx + s) for s in range(6)]
+    calls = []
+    declared = []                         # declared need of each ticket
+    for k in range(n_ops):
+        r = float(u[0][k])
+        if not declared or r < p_declare:
+            w = float(u[1][k])
+            if w < 0.04:
+                need = 0
+            elif w < 0.07:
+                need = budget
+            else:
+                need = int(math.floor(math.exp(float(u[2][k]) * math.log(max(budget // 2, 2)))))
+            prio = int(math.floor(float(u[3][k]) * prio_levels))
+            calls.append(("declare", need, prio))
+            declared.append(need)
+            continue
+        t = int(math.floor(float(u[4][k]) * len(declared)))
+        if r < p_declare + p_release:
+            v = float(u[5][k])
+            need = declared[t]
+            if v < 0.35 or need < 2:
+                nbytes = 0
+            elif v < 0.85:
+                nbytes = 1 + int(math.floor((v - 0.35) / 0.5 * (need - 1)))
+            else:
+                nbytes = need + 1 + int(math.floor((v - 0.85) * 1e4))
+            calls.append(("release", t, nbytes))
+        else:
+            calls.append(("cancel", t))
+    return calls
