@@ -141,7 +141,11 @@ typedef struct sg_run_stats {
     uint64_t wait_p50_ns, wait_p99_ns;             /* grant - arrival, nearest rank */
     uint64_t turnaround_p50_ns, turnaround_p99_ns; /* release - arrival           */
     uint64_t peak_used;        /* peak granted bytes                           */
-    uint64_t frag_waits;       /* count-fit requests that could not be placed  */
+    uint64_t frag_waits;       /* passes that ended blocked by fragmentation: the
+                                  waiter the policy serves next fits the free
+                                  byte count but no free extent holds it (a
+                                  diagnostic of this library; the paper counts
+                                  bytes only) */
     uint64_t launches;         /* kernels this call launched                   */
     uint64_t passes;           /* notification passes run by the engine        */
     uint32_t jobs_done, jobs_failed;
@@ -191,11 +195,13 @@ int sg_try(sg_ctx* ctx, sg_ticket t, sg_grant* out);
 int sg_wait(sg_ctx* ctx, sg_ticket t, uint64_t timeout_ns, sg_grant* out);
 
 /* Post-free (Sec. IV, postCudaFree): enqueue on `stream`, after the work
- * that uses the memory, the release of `bytes` declared bytes of ticket t
- * (0 = everything it holds, the paper's bytes == 0 form; a smaller amount
- * shrinks the grant from its end). Freeing notifies the waiters through
- * the policy pass on the device. SG_ERR_INVALID if t holds no memory (the
- * paper's check that the bytes were pre-allocated). */
+ * that uses the memory, the release of `bytes` declared bytes of ticket t.
+ * 0, or at least the bytes t still holds, frees everything (the paper's
+ * bytes == 0 form); a smaller amount shrinks the grant from its end: t
+ * keeps its first (held - bytes) bytes, rounded up to the granule, at the
+ * same offset. Freeing notifies the waiters through the policy pass on the
+ * device. SG_ERR_INVALID if t holds no memory (the paper's check that the
+ * bytes were pre-allocated), including any release after a full one. */
 int sg_release(sg_ctx* ctx, sg_ticket t, uint64_t bytes, void* stream);
 
 /* Withdraw a request that is still waiting (what an expired blocking
@@ -215,13 +221,18 @@ int sg_poll_grants(sg_ctx* ctx, uint32_t* cursor, sg_ticket* out, uint32_t max, 
 
 /* Run job `job` in the memory granted to ticket t, on `stream`: its input
  * generator, then its kernel, whose last block releases the ticket
- * (wake-on-release without a host round trip). tables_dev: device array of
+ * (wake-on-release without a host round trip). This is the application's
+ * part of the life cycle between pre-allocation and post-free (Sec. VI,
+ * "Concurrent Execution of Individual Applications": pre-allocation before
+ * the allocations, post-free after the release of memory). tables_dev: device array of
  * 64-entry uint64 Poisson tables (SpMV jobs), may be NULL otherwise. */
 int sg_launch(sg_ctx* ctx, sg_ticket t, const sg_job* job, const uint64_t* tables_dev,
               void* stream);
 
-/* Run a whole trace: declare every job (at t=0 or at its arrival time),
- * launch each as it is granted on a free stream slot, under the start rules
+/* Run a whole trace, the many co-scheduled instances of the paper's
+ * evaluation (Sec. VI, "Workloads Comprising Multiple Applications"): declare
+ * every job (at t=0 or at its arrival time), launch each as it is granted on
+ * a free stream slot, under the start rules
  * of sg_config.run_flags (SpMV and GEMM in turn, long jobs one at a time),
  * until every job is released. Ticket i is job i. jobs/log: device buffers (host buffers with
  * SG_RUN_HOST_IO, copied in and out inside the call). log receives one

@@ -116,7 +116,7 @@ __host__ __device__ inline uint64_t phase_chunks(const sg_job& j, uint32_t ph) {
 // Called by one thread: reserve and publish the chunks of one phase.
 __device__ void push_phase(const BatchDev& B, uint32_t job, uint32_t ph) {
   const uint64_t cnt = phase_chunks(B.jobs[job], ph);
-  stcg(B.left + job, (uint32_t)cnt);
+  st_gpu(B.left + job, (uint32_t)cnt);
   __threadfence();
   const uint64_t base = atomicAdd(&B.ctr[1], (unsigned long long)cnt);
   if (base + cnt > B.total) {
@@ -140,7 +140,7 @@ __device__ void push_phase_warp(const BatchDev& B, uint32_t job, uint32_t ph) {
   const uint64_t cnt = phase_chunks(B.jobs[job], ph);
   unsigned long long base = 0;
   if (lane_id() == 0) {
-    stcg(B.left + job, (uint32_t)cnt);
+    st_gpu(B.left + job, (uint32_t)cnt);
     __threadfence();
     base = atomicAdd(&B.ctr[1], (unsigned long long)cnt);
     if (base + cnt > B.total) atomicOr(B.err, ERR_CAP);
@@ -155,7 +155,7 @@ __device__ void push_phase_warp(const BatchDev& B, uint32_t job, uint32_t ph) {
     B.items[base + i] = it;
   }
   __threadfence();                            // each lane's items before its sequence words
-  for (uint64_t i = lane_id(); i < cnt; i += 32) stcg(B.seq + base + i, (uint32_t)(base + i + 1));
+  for (uint64_t i = lane_id(); i < cnt; i += 32) st_gpu(B.seq + base + i, (uint32_t)(base + i + 1));
   __syncwarp();
 }
 
@@ -175,7 +175,7 @@ __device__ bool spin_until(const BatchDev& B, Pred pred) {
   for (uint32_t it = 0;; it++) {
     if (pred()) return true;
     if ((it & 15) == 15) {
-      if (ldcg(B.err) != 0) return false;
+      if (ld_gpu(B.err) != 0) return false;
       const uint64_t now = globaltimer_ns();
       if (t0 == 0) t0 = now;
       else if (now - t0 > kBatchWaitNs) { atomicOr(B.err, ERR_LOCK); return false; }
@@ -192,11 +192,11 @@ __device__ bool hand_over(const BatchDev& B, const Eng& E, GrantQueue* Q, uint32
   if (lane_id() == 0) {
     for (uint32_t p = from; p < to && ok; p++) {
       const uint32_t j = eld(E, E.dev_ring + p % B.n);
-      stcg(B.offset + j, eld(E, reinterpret_cast<const uint64_t*>(E.rec + j) + 3));   // sg_record.offset
+      st_gpu(B.offset + j, eld(E, reinterpret_cast<const uint64_t*>(E.rec + j) + 3));   // sg_record.offset
       volatile GrantQueue* vq = Q;
       const uint32_t t = vq->tail;
       if (t >= B.n) { atomicOr(B.err, ERR_CAP); ok = false; break; }   // cannot happen: n grants
-      stcg(B.glist + t, j);
+      st_gpu(B.glist + t, j);
       __threadfence();                        // offset and list entry before the tail moves
       vq->tail = t + 1;
     }
@@ -215,9 +215,9 @@ __device__ void engine_service(const BatchDev& B, GrantQueue* Q) {
   for (uint32_t r = 0; r < B.n && s.err == 0 && ok; r++) {
     uint32_t j = 0;
     if (lane_id() == 0) {                     // the r-th finished job
-      ok = spin_until(B, [&] { return ldcg(B.comp_seq + r) == r + 1; });
+      ok = spin_until(B, [&] { return ld_gpu(B.comp_seq + r) == r + 1; });
       __threadfence();
-      if (ok) j = ldcg(B.comp + r);
+      if (ok) j = ld_gpu(B.comp + r);
     }
     ok = __shfl_sync(SG_FULL, (int)ok, 0) != 0;
     j = __shfl_sync(SG_FULL, j, 0);
@@ -251,7 +251,7 @@ __device__ void publish_service(const BatchDev& B, GrantQueue* Q) {
     c = __shfl_sync(SG_FULL, c, 0);
     if (!have) break;
     __threadfence();
-    push_phase_warp(B, ldcg(B.glist + c), 0);
+    push_phase_warp(B, ld_gpu(B.glist + c), 0);
   }
 }
 
@@ -263,9 +263,9 @@ __device__ int pop(const BatchDev& B, Item* out) {
   uint64_t t0 = 0;
   unsigned ns = 32;
   for (uint32_t it = 0;; it++) {
-    if (ldcg(B.seq + pos) == want) break;
+    if (ld_gpu(B.seq + pos) == want) break;
     if ((it & 15) == 15) {
-      if (ldcg(B.err) != 0) return -1;
+      if (ld_gpu(B.err) != 0) return -1;
       const uint64_t now = globaltimer_ns();
       if (t0 == 0) t0 = now;
       else if (now - t0 > kBatchWaitNs) {
@@ -278,7 +278,7 @@ __device__ int pop(const BatchDev& B, Item* out) {
   }
   __threadfence();
   const uint64_t* src = reinterpret_cast<const uint64_t*>(B.items + pos);
-  uint64_t w0 = ldcg(src), w1 = ldcg(src + 1);
+  uint64_t w0 = ld_gpu(src), w1 = ld_gpu(src + 1);
   out->job = (uint32_t)w0;
   out->phase = (uint32_t)(w0 >> 32);
   out->chunk = w1;
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchDev B) {
     if (action[gi] != 1) break;
     const Item it = cur[gi];
     const sg_job& job = B.jobs[it.job];
-    char* base = B.pool + ldcg(B.offset + it.job);
+    char* base = B.pool + ld_gpu(B.offset + it.job);
     const bool keep = B.keep != nullptr;
     const uint32_t nph = job_phases(job, keep);
     const bool digest = keep && it.phase == nph - 1;
@@ -498,7 +498,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchDev B) {
       } else if (B.online) {
         if (g.t() == 0) {                             // hand the job to the engine warp
           const uint64_t r = atomicAdd(&B.ctr[3], 1ull);
-          stcg(B.comp + r, it.job);
+          st_gpu(B.comp + r, it.job);
           __threadfence();
           atomicExch(B.comp_seq + r, (uint32_t)(r + 1));
           atomicAdd(&B.ctr[2], 1ull);

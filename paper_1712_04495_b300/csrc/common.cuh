@@ -1,5 +1,5 @@
-// Shared device helpers: SplitMix64 element generator, clock, cache-global
-// memory access. No scheduling logic here.
+// Shared device helpers: SplitMix64 element generator, clock, GPU-scope
+// memory access and fences. No scheduling logic here.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -64,18 +64,22 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
-// L2-coherent accesses (ld/st .cg) for state shared by concurrently running
-// kernels. The "memory" clobber keeps the compiler from moving them across
-// other memory operations and warp barriers: a lane must see what another
-// lane stored before a __syncwarp.
-#define SG_LDCG(T, PTX, C)                                                            \
-  __device__ __forceinline__ T ldcg(const T* p) {                                     \
-    T v;                                                                              \
-    asm volatile("ld.global.cg." PTX " %0, [%1];" : "=" C(v) : "l"(p) : "memory");   \
-    return v;                                                                         \
-  }                                                                                   \
-  __device__ __forceinline__ void stcg(T* p, T v) {                                   \
-    asm volatile("st.global.cg." PTX " [%0], %1;" ::"l"(p), C(v) : "memory");         \
+// Accesses to state shared by kernels running on different SMs: strong
+// (relaxed, GPU scope) loads and stores. A weak load may be served from a
+// copy that the memory model lets go stale until the reading thread itself
+// synchronises; a relaxed load at GPU scope reads the coherent value. Lock
+// and flag protocols add the fences that order them (fence.acq_rel.gpu).
+// The "memory" clobber keeps the compiler from moving them across other
+// memory operations and warp barriers: a lane must see what another lane
+// stored before a __syncwarp.
+#define SG_LDCG(T, PTX, C)                                                              \
+  __device__ __forceinline__ T ld_gpu(const T* p) {                                     \
+    T v;                                                                                \
+    asm volatile("ld.relaxed.gpu.global." PTX " %0, [%1];" : "=" C(v) : "l"(p) : "memory"); \
+    return v;                                                                           \
+  }                                                                                     \
+  __device__ __forceinline__ void st_gpu(T* p, T v) {                                   \
+    asm volatile("st.relaxed.gpu.global." PTX " [%0], %1;" ::"l"(p), C(v) : "memory");  \
   }
 SG_LDCG(unsigned int, "u32", "r")
 SG_LDCG(int, "s32", "r")
@@ -84,6 +88,9 @@ SG_LDCG(long, "s64", "l")
 SG_LDCG(unsigned long long, "u64", "l")
 SG_LDCG(long long, "s64", "l")
 #undef SG_LDCG
+
+// fence.acq_rel at GPU scope, executed by the calling thread
+__device__ __forceinline__ void fence_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 
 }  // namespace sg

@@ -82,10 +82,10 @@ __global__ void k_declare(Eng shared, uint32_t first, uint32_t count, const sg_j
     int32_t pr = jobs ? (int32_t)jobs[t].prio : prio;
     uint64_t g = exclusive ? s.budget : round_need(raw, s.granule);
     if (lane_id() == 0) {
-      stcg(E.need_g + t, g);
-      stcg(E.need_raw + t, exclusive ? s.budget : raw);
-      stcg(E.prio + t, pr);
-      stcg(E.blk_done + t, 0u);
+      st_gpu(E.need_g + t, g);
+      st_gpu(E.need_raw + t, exclusive ? s.budget : raw);
+      st_gpu(E.prio + t, pr);
+      st_gpu(E.blk_done + t, 0u);
     }
     __syncwarp();
     op_declare(E, s, t, globaltimer_ns(), -1, nullptr, nullptr, nullptr);
@@ -229,6 +229,7 @@ struct sg_ctx {
   std::mutex mu;
   uint32_t next_ticket = 0;
   std::vector<uint8_t> rel_enq;  // a full release is already enqueued
+  std::vector<uint64_t> held_raw;  // declared bytes a ticket holds after the partial releases enqueued
   std::vector<uint32_t> free_tickets;   // finished tickets that sg_declare may reuse
   std::vector<uint8_t> in_free;
   cudaStream_t ctrl = nullptr;
@@ -309,6 +310,7 @@ extern "C" int sg_init(sg_ctx** out, void* dev_pool, uint64_t pool_bytes, const 
   c->run_flags = d.run_flags;
   c->phase_jobs = d.phase_jobs ? d.phase_jobs : 64;
   c->rel_enq.assign(cap, 0);
+  c->held_raw.assign(cap, 0);
   c->in_free.assign(cap, 0);
   int rc = SG_ERR_CUDA;
   do {
@@ -424,6 +426,7 @@ extern "C" int sg_declare(sg_ctx* c, uint64_t need, int32_t priority, sg_ticket*
     c->rel_enq[t] = 0;
   }
   c->h_rec[t].status = SG_ST_PENDING;
+  c->held_raw[t] = need;
   k_declare<<<1, 32, 0, c->ctrl>>>(c->eng, t, 1, nullptr, need, priority, 0);
   if (cudaGetLastError() != cudaSuccess) return SG_ERR_CUDA;
   *out = t;
@@ -589,7 +592,11 @@ extern "C" int sg_release(sg_ctx* c, sg_ticket t, uint64_t bytes, void* stream) 
   if (!c || t >= c->cap) return SG_ERR_INVALID;
   std::lock_guard<std::mutex> lk(c->mu);
   if ((uint32_t)c->h_rec[t].status != SG_ST_RUNNING || c->rel_enq[t]) return SG_ERR_INVALID;
-  if (bytes == 0) c->rel_enq[t] = 1;
+  // the device frees everything for 0 or for at least what is held; a
+  // later release of the same ticket is then refused here, before it could
+  // reach the device
+  if (bytes == 0 || bytes >= c->held_raw[t]) c->rel_enq[t] = 1;
+  else c->held_raw[t] -= bytes;
   k_release<<<1, 32, 0, (cudaStream_t)stream>>>(c->eng, t, bytes);
   return cudaGetLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
 }

@@ -21,7 +21,8 @@
 // byte count (budget - used) and can be placed.
 //
 // State accesses: a live engine is shared by kernels on many SMs and every
-// access goes through L2 (ld/st .cg). A replay owns its state in one warp for
+// access is a strong GPU-scope load or store (ld/st .relaxed.gpu) made under
+// the lock's acquire and release fences. A replay owns its state in one warp for
 // the whole kernel, so it uses plain (L1-cached) accesses; `Eng::owned` says
 // which, and kernels set it in a local copy so the choice is made at compile
 // time.
@@ -70,11 +71,11 @@ __device__ __forceinline__ Eng eng_live(Eng E) { E.owned = 0; return E; }
 __device__ __forceinline__ Eng eng_owned(Eng E) { E.owned = 1; return E; }
 
 template <typename T>
-__device__ __forceinline__ T eld(const Eng& E, const T* p) { return E.owned ? *p : ldcg(p); }
+__device__ __forceinline__ T eld(const Eng& E, const T* p) { return E.owned ? *p : ld_gpu(p); }
 template <typename T>
 __device__ __forceinline__ void est(const Eng& E, T* p, T v) {
   if (E.owned) *p = v;
-  else stcg(p, v);
+  else st_gpu(p, v);
 }
 
 // granule-rounded request; a request of 0 bytes still takes a granule
@@ -150,6 +151,15 @@ __device__ __forceinline__ void sess_store(const Eng& E, const Sess& s) {
 // ------------------------------------------------------------------ lock
 // Spin on the engine lock with a bounded wait (globaltimer); on expiry the
 // caller gets false and the error flag is raised. Warp-uniform result.
+//
+// Every lane reads and writes the state, not only lane 0 that takes the
+// lock, so every lane must be ordered after the acquisition and before the
+// release. A shuffle carries a value between lanes but orders no memory, so
+// after lane 0's acquiring fence the warp meets at a __syncwarp (a barrier
+// that orders memory among its lanes) and each lane then runs its own
+// acquire fence before its first load of the state. Unlocking mirrors it:
+// each lane fences its own stores, the warp meets, and only then does lane 0
+// store the free lock word.
 __device__ __forceinline__ bool eng_lock(const Eng& E, uint64_t limit_ns = 2000000000ull) {
   int ok = 0;
   if (lane_id() == 0) {
@@ -165,16 +175,19 @@ __device__ __forceinline__ bool eng_lock(const Eng& E, uint64_t limit_ns = 20000
       atomicOr(&E.hdr->err, ERR_LOCK);
       if (E.pub_hdr) atomicOr_system(&E.pub_hdr[1], ERR_LOCK);
     }
-    __threadfence();
+    fence_gpu();
   }
   ok = __shfl_sync(SG_FULL, ok, 0);
+  __syncwarp();
+  fence_gpu();
   return ok != 0;
 }
 
 __device__ __forceinline__ void eng_unlock(const Eng& E) {
+  fence_gpu();
   __syncwarp();
   if (lane_id() == 0) {
-    __threadfence();
+    fence_gpu();
     atomicExch(&E.hdr->lock, 0u);
   }
   __syncwarp();
@@ -855,7 +868,7 @@ __device__ __forceinline__ void replay_run(const Eng& state, const sg_job* __res
     stats[0] = s.peak;
     stats[1] = s.frag;
     stats[2] = s.passes;
-    stats[3] = s.err | ldcg(&E.hdr->err);
+    stats[3] = s.err | ld_gpu(&E.hdr->err);
   }
 }
 

@@ -14,8 +14,8 @@ def build(out_dir: str) -> str:
     with open(os.path.join(ROOT, "paper_1712_04495_b300", "csrc", "engine.cuh")) as f:
         text = f.read()
     # every state access through the shim's accessors, owned state included
-    for old, new in (("return E.owned ? *p : ldcg(p);", "return ldcg(p);"),
-                     ("if (E.owned) *p = v;\n  else stcg(p, v);", "stcg(p, v);")):
+    for old, new in (("return E.owned ? *p : ld_gpu(p);", "return ld_gpu(p);"),
+                     ("if (E.owned) *p = v;\n  else st_gpu(p, v);", "st_gpu(p, v);")):
         assert text.count(old) == 1, old
         text = text.replace(old, new)
     with open(os.path.join(src, "engine.cuh"), "w") as f:

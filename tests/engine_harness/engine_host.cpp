@@ -147,10 +147,10 @@ void eh_declare(void* p, uint32_t t, uint64_t need, int32_t prio) {
     if (!eng_lock(E)) return;
     Sess s = sess_load(E);
     if (lane_id() == 0) {
-      stcg(E.need_g + t, round_need(need, s.granule));
-      stcg(E.need_raw + t, need);
-      stcg(E.prio + t, prio);
-      stcg(E.blk_done + t, 0u);
+      st_gpu(E.need_g + t, round_need(need, s.granule));
+      st_gpu(E.need_raw + t, need);
+      st_gpu(E.prio + t, prio);
+      st_gpu(E.blk_done + t, 0u);
     }
     __syncwarp();
     op_declare(E, s, t, globaltimer_ns(), -1, nullptr, nullptr, nullptr);

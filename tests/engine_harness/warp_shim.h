@@ -69,9 +69,10 @@ inline uint64_t lane_exchange(uint64_t v, uint32_t src) {
 }
 
 inline uint64_t globaltimer_ns() { return g_clock.fetch_add(1); }
+inline void fence_gpu() { __atomic_thread_fence(__ATOMIC_SEQ_CST); }
 
 template <typename T>
-inline T ldcg(const T* p) {
+inline T ld_gpu(const T* p) {
   static_assert(sizeof(T) <= 8, "word access");
   for (auto it = t_pending.rbegin(); it != t_pending.rend(); ++it) {
     if (it->p == (const void*)p) {
@@ -85,7 +86,7 @@ inline T ldcg(const T* p) {
   return r;
 }
 template <typename T>
-inline void stcg(T* p, T v) {
+inline void st_gpu(T* p, T v) {
   PendingStore x{(void*)p, 0, (uint32_t)sizeof(T)};
   memcpy(&x.v, &v, sizeof(T));
   t_pending.push_back(x);
