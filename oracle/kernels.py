@@ -86,6 +86,40 @@ def spmv_sampled(key: int, rows: int, table, sample_rows):
     return y, mag, ptr
 
 
+def spmv_sampled_streamed(key: int, rows: int, table, sample_rows, chunk: int = 1 << 22):
+    """spmv_sampled for matrices too large to hold row_ptr on the host: the
+    row lengths are summed chunk by chunk, and only the chosen rows' start
+    and end offsets are kept. Returns y, |.|-sums, starts, ends and nnz."""
+    sample_rows = np.asarray(sample_rows, dtype=np.int64)
+    starts = np.zeros(len(sample_rows), dtype=np.int64)
+    ends = np.zeros(len(sample_rows), dtype=np.int64)
+    kl = tg.stream_key(key, 1)
+    base = 0
+    for s in range(0, rows, chunk):
+        e = min(rows, s + chunk)
+        lens = tg.row_lengths(kl, np.arange(s, e, dtype=np.uint64), table)
+        sel = (sample_rows >= s) & (sample_rows < e)
+        if np.any(sel):
+            cs = np.zeros(e - s + 1, dtype=np.int64)
+            np.cumsum(lens, out=cs[1:])
+            starts[sel] = base + cs[sample_rows[sel] - s]
+            ends[sel] = base + cs[sample_rows[sel] - s + 1]
+        base += int(lens.sum())
+    kx = tg.stream_key(key, 4)
+    kc = tg.stream_key(key, 2)
+    kv = tg.stream_key(key, 3)
+    y = np.zeros(len(sample_rows))
+    mag = np.zeros(len(sample_rows))
+    for t in range(len(sample_rows)):
+        e = np.arange(starts[t], ends[t], dtype=np.uint64)
+        col = tg.spmv_columns(kc, e, rows)
+        val = tg.spmv_values(kv, e).astype(np.float64)
+        x = tg.uniform_pm1_f32(tg.sm64_at(kx, col.astype(np.uint64))).astype(np.float64)
+        y[t] = float(np.sum(val * x))
+        mag[t] = float(np.sum(np.abs(val * x)))
+    return y, mag, starts, ends, base
+
+
 # -------------------------------------------------------------------- GEMM
 def gemm_a(key: int, m: int, k: int, rows=None) -> np.ndarray:
     """A[i, :] as fp64 values of the bf16 inputs (rows defaults to all m)."""

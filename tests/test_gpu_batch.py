@@ -1,11 +1,14 @@
 """Batching: a trace admitted as a whole by the device engine (replay plan)
 and run as one CUDA graph and by the persistent grouped kernel. Each job's
 output must equal the one-launch-per-job run (output digests), triads
-bit-exact against the oracle."""
+bit-exact against the oracle; in a pool that holds every job at once, the
+output arrays of each kind and size (the batch kernel's own tcgen05 GEMM
+tiles and chunked SpMV included) are compared with the oracle."""
 import numpy as np
 import pytest
 import torch
 
+from job_outputs import check_job_output, pick_jobs
 from oracle import kernels as K
 from paper_1712_04495_b300 import tracegen as tg
 
@@ -150,3 +153,46 @@ def test_online_batch_rejects_a_job_that_never_fits():
     with pytest.raises(abi.SgError):
         abi.sg_batch_build_online(pool.data_ptr(), pool.numel(), jobs, tab.data_ptr(), "first_fit")
 
+
+def test_batch_outputs_match_the_oracle():
+    """The 10,000 tiny jobs in a pool that holds them all, so no job's memory
+    is reused and every output stays in its grant: the persistent grouped
+    kernel (planned and admitting online) and the CUDA graph each run the
+    batch on a cleared pool, and the outputs of the smallest, largest and
+    spread-out jobs of every kind (every GEMM size) are compared with the
+    oracle array by array."""
+    from paper_1712_04495_b300 import abi, runtime
+    tr = tg.trace_c4()
+    need_g = (tr.jobs["need"].astype(np.int64) + 255) // 256 * 256
+    budget = int(need_g.sum()) + MIB
+    pool = torch.zeros(budget, dtype=torch.uint8, device="cuda")
+    tab = runtime.device_tables(tr)
+    picks = pick_jobs(tr.jobs, per_kind=8)
+    assert {int(k) for k in tr.jobs["kind"][picks]} == {tg.KIND_TRIAD, tg.KIND_SPMV, tg.KIND_GEMM}
+    pl = runtime.Planned(pool, tr.jobs, tab, "first_fit", keep=False, budget=budget)
+    assert pl.plan_stats["err"] == 0
+    assert np.all(pl.plan["grant_t"] == 0)                 # everything granted at once
+    offs = pl.plan["offset"].astype(np.int64)
+    errs = {}
+    for name, run in (("batch", pl.run_batch), ("graph", pl.run_graph)):
+        pool.zero_()
+        assert run() == abi.SG_OK
+        torch.cuda.synchronize()
+        if name == "batch":
+            rc, done, err = pl.batch_status()
+            assert (rc, err, done) == (abi.SG_OK, 0, len(tr))
+        for j in picks:
+            errs[(name, j)] = check_job_output(pool, int(offs[j]), tr.jobs[j], tr.tables)
+    pl.close()
+    ob = runtime.OnlineBatch(pool, tr.jobs, tab, "first_fit", keep=False, budget=budget)
+    pool.zero_()
+    assert ob.run() == abi.SG_OK
+    torch.cuda.synchronize()
+    rc, done, err = ob.status()
+    assert (rc, err, done) == (abi.SG_OK, 0, len(tr))
+    rec = ob.records()
+    for j in picks:
+        check_job_output(pool, int(rec["offset"][j]), tr.jobs[j], tr.tables)
+    ob.close()
+    gemm_err = max(v for (n, j), v in errs.items() if tr.jobs["kind"][j] == tg.KIND_GEMM)
+    assert gemm_err < 1e-4                                   # FP32 accumulation of exact bf16 products

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 import torch
 
+from job_outputs import check_job_output
 from oracle import invariants
 from oracle import kernels as K
 from paper_1712_04495_b300 import tracegen as tg
@@ -267,4 +268,14 @@ def test_serving_results_equal_alone_and_in_the_mix(overlap):
     rc, _, keep_alone, _ = s.run_trace(d_jobs, d_tab, abi.SG_RUN_SATURATED | abi.SG_RUN_EXCLUSIVE, keep=True)
     assert rc == abi.SG_OK
     assert torch.equal(keep_mix, keep_alone)
+    # and each request's output, run alone through the same runner, is the
+    # oracle's: the served result equals it through the digests
+    for j in range(len(tr)):
+        one = tr.jobs[[j]].copy()
+        one["arrival_ns"] = 0
+        rc, log1, keep1, _ = s.run_trace(rt.to_device(one), d_tab, abi.SG_RUN_SATURATED, keep=True)
+        assert rc == abi.SG_OK
+        torch.cuda.synchronize()
+        assert int(keep1[0].item()) == int(keep_mix[j].item()), j
+        check_job_output(s.pool, int(rt.records(log1)["offset"][0]), tr.jobs[j], tr.tables)
     s.shutdown()

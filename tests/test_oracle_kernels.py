@@ -56,6 +56,16 @@ def test_spmv_sampled_equals_full():
     assert np.allclose(ms, mag[rows], rtol=1e-14)
 
 
+def test_spmv_streamed_equals_sampled():
+    table = tg.poisson_cdf_table(16.0)
+    rows = 5000
+    sample = np.array([0, 1, 17, 2047, 2048, 4095, 4999])
+    ys, ms, ptr = K.spmv_sampled(3, rows, table, sample)
+    y2, m2, st, en, nnz = K.spmv_sampled_streamed(3, rows, table, sample, chunk=1024)
+    assert np.array_equal(ys, y2) and np.array_equal(ms, m2)
+    assert np.array_equal(st, ptr[sample]) and np.array_equal(en, ptr[sample + 1]) and nnz == ptr[-1]
+
+
 def test_gemm_exact_for_small_k():
     # bf16 products are exact in fp64 and sums of 32 of them stay exact:
     # compare with rational arithmetic
