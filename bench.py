@@ -344,8 +344,87 @@ def kernel_roofline(torch, abi, peaks):
                               "the L1/L2 sector rate of random gathers, with HBM traffic equal to the "
                               "algorithmic bytes",
                    "gathers_per_s": nnz / (ms * 1e-3)}
+    # the input generators, alone at the same sizes (instruction-issue and ALU bound)
+    tab_ptr = tab.data_ptr()
     del base
+    base = torch.empty(lay["total"], dtype=torch.uint8, device="cuda")
+    p = base.data_ptr()
+    A = torch.empty(8192 * 8192, dtype=torch.int16, device="cuda")
+    B = torch.empty(8192 * 8192, dtype=torch.int16, device="cuda")
+    buf = torch.empty(2 * n, dtype=torch.float32, device="cuda")
+    gens = {"spmv": (lambda: abi.sg_gen_spmv(p, rows, cap, tab_ptr, 5, 0, s.cuda_stream), nnz, "non-zero"),
+            "gemm": (lambda: abi.sg_gen_gemm(A.data_ptr(), B.data_ptr(), 8192, 8192, 8192, 42, s.cuda_stream),
+                     2 * 8192 * 8192, "bf16 element"),
+            "triad": (lambda: abi.sg_gen_triad(buf[:n].data_ptr(), buf[n:].data_ptr(), n, 7, s.cuda_stream),
+                      n, "element")}
+    out["generators"] = {}
+    for name, (fn, units, what) in gens.items():
+        fn()
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(5):
+            fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        out["generators"][name] = {"ms": ms, "ns_per_unit": 1e6 * ms / units, "unit": what}
+    del base, A, B, buf
     torch.cuda.synchronize()
+    return out
+
+
+def makespan_bound(trace: tg.Trace, kr: dict, peaks: dict, serial_ms: float) -> dict:
+    """Lower bounds on a step's makespan, against the measured exclusive-serial one.
+
+    disjoint_resources: the step's work on each resource at that resource's
+    rate, if every kind's bottleneck were a resource of its own and all of it
+    overlapped: HBM bytes (kernels' algorithmic bytes plus the generators'
+    writes) at the measured copy bandwidth; GEMM flops at the sustained bf16
+    peak; SpMV gathers (expected rows x lambda) at the SpMV's own gather rate
+    measured above; generator time at the generators' measured rates.
+    unit_counters: the largest per-unit busy time of a step from ncu unit
+    counters of each kernel and its time per step in the launch list (a
+    committed profile): no schedule packs a unit beyond 100%."""
+    hbm, flops, gathers, gen_ms = 0.0, 0.0, 0.0, 0.0
+    g = kr["generators"]
+    for job in trace.jobs:
+        kind = int(job["kind"])
+        if kind == tg.KIND_TRIAD:
+            nn = int(job["p0"])
+            hbm += tg.triad_alg_bytes(nn) + 8 * nn
+            gen_ms += g["triad"]["ns_per_unit"] * nn * 1e-6
+        elif kind == tg.KIND_SPMV:
+            rows = int(job["p0"])
+            nnz = rows * trace.lambdas[int(job["p2"])]
+            hbm += tg.spmv_alg_bytes(rows, int(nnz)) + 8 * nnz + 4 * (rows + 1) + 4 * rows
+            gathers += nnz
+            gen_ms += g["spmv"]["ns_per_unit"] * nnz * 1e-6
+        else:
+            m = int(job["p0"])
+            hbm += 2 * m * m + 2 * m * m + 4 * m * m + 4 * m * m
+            flops += tg.gemm_flops(m, m, m)
+            gen_ms += g["gemm"]["ns_per_unit"] * 2 * m * m * 1e-6
+    parts = {"hbm_ms": hbm / (peaks["hbm_gbs"] * 1e9) * 1e3,
+             "tensor_ms": flops / ((peaks["bf16_tflops_sustained"] or peaks["bf16_tflops"]) * 1e12) * 1e3,
+             "gathers_ms": gathers / kr["spmv"]["gathers_per_s"] * 1e3,
+             "generators_ms": gen_ms}
+    disjoint = max(parts.values())
+    out = {"exclusive_serial_ms": serial_ms,
+           "disjoint_resources": {"ms": disjoint, "ratio_vs_serial": disjoint / serial_ms, **parts}}
+    p = os.path.join(ROOT, "profiles", "units_per_kernel_mixed256.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        busy = {}
+        for u in d["units"]:
+            tot = 0.0
+            for k, t in d["per_step_ms"].items():
+                ref = d["same_units_as"].get(k, k)
+                tot += t * d["pct"][ref][u] / 100.0
+            busy[u] = tot
+        u_max = max(busy, key=busy.get)
+        out["unit_counters"] = {"ms": busy[u_max], "unit": u_max, "ratio_vs_serial": busy[u_max] / serial_ms,
+                                "source": "ncu unit counters per kernel x kernel time per step of the launch list"}
     return out
 
 
@@ -997,6 +1076,7 @@ def main():
         # the job kernels timed alone, before the long extra sections heat the GPU
         kr = kernel_roofline(torch, abi, peaks)
         extra["kernels"] = kr
+        extra["makespan_bound"] = makespan_bound(trace, kr, peaks, ms["exclusive_serial"])
         if not args.no_extras:
             extra["lifecycle"] = lifecycle_section(torch, abi, runtime)
             extra["client_server"] = client_server_section(torch, abi, runtime)
