@@ -265,11 +265,14 @@ int sg_replay(const sg_job* jobs_dev, uint32_t n, uint64_t budget, uint64_t gran
  * library's device image, which every GPU that loads the library holds
  * until the process exits. Up to SG_REPLAY_NOALLOC_MAX_JOBS jobs; larger
  * traces get SG_ERR_TOO_LARGE and nothing runs. The first call on each
- * device looks up the array's device address (make that first call before
- * any stream capture). All calls share the array and it keeps the last
- * call's contents; the replay initialises what it reads, so no clearing is
- * needed, but calls that overlap on the GPU race on it: order them on one
- * stream. */
+ * device (and again after the device's context was reset) looks up the
+ * array's device address; make that first call before any stream capture:
+ * while `stream` is being captured the lookup is refused with
+ * SG_ERR_INVALID. All calls share the array and it keeps the last call's
+ * contents; the replay initialises what it reads, so no clearing is needed,
+ * but calls that overlap on the GPU race on it: order them on one stream.
+ * Like sg_replay, a call that finds a CUDA error already pending on the
+ * thread reports SG_ERR_CUDA. */
 #define SG_REPLAY_NOALLOC_MAX_JOBS 16384u
 int sg_replay_noalloc(const sg_job* jobs_dev, uint32_t n, uint64_t budget, uint64_t granule,
                       uint32_t policy, uint32_t flags, uint32_t exclusive, sg_record* log_dev,

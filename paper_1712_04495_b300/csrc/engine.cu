@@ -15,6 +15,7 @@
 #include <thread>
 #include <vector>
 
+#include <cuda.h>
 #include <nvtx3/nvToolsExt.h>
 
 #include "engine.cuh"
@@ -915,22 +916,56 @@ constexpr uint64_t kNoAllocBytes = 2048ull * 1024;   // >= sg_replay_workspace_b
 static __device__ __align__(256) unsigned char g_replay_scratch[kNoAllocBytes];
 
 constexpr int kMaxDevices = 128;
-std::mutex g_scratch_mu;
-void* g_scratch_ptr[kMaxDevices] = {};
+static_assert(kNoAllocMaxJobs == SG_REPLAY_NOALLOC_MAX_JOBS, "the header states the limit");
 
-// Device address of the array on the current device, looked up once per
-// device. In host code the array's name is only a stand-in for it.
-int scratch_address(void** out) {
+// The array's device address, looked up once per device and context: a
+// context torn down and made again (cudaDeviceReset) loads the module anew,
+// and the address is looked up again for the new context.
+struct ScratchAddr {
+  void* ctx = nullptr;
+  void* ptr = nullptr;
+};
+std::mutex g_scratch_mu;
+ScratchAddr g_scratch[kMaxDevices];
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrentFn>(p);
+  });
+  return fn;
+}
+
+// Device address of the array on the current device. In host code the
+// array's name is only a stand-in for it. The lookup is a set-up step: it is
+// refused (SG_ERR_INVALID) while `stream` is being captured into a graph.
+int scratch_address(cudaStream_t stream, void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return SG_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return SG_ERR_INVALID;
+  CtxGetCurrentFn get = ctx_get_current();
+  CUcontext ctx = nullptr;
+  if (!get || get(&ctx) != CUDA_SUCCESS || !ctx) return SG_ERR_CUDA;
   std::lock_guard<std::mutex> g(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_replay_scratch) != cudaSuccess || !p) return SG_ERR_CUDA;
-    g_scratch_ptr[dev] = p;
+  ScratchAddr& a = g_scratch[dev];
+  if (a.ptr && a.ctx == (void*)ctx) {
+    *out = a.ptr;
+    return SG_OK;
   }
-  *out = g_scratch_ptr[dev];
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) return SG_ERR_CUDA;
+  if (cap != cudaStreamCaptureStatusNone) return SG_ERR_INVALID;
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_replay_scratch) != cudaSuccess || !p) return SG_ERR_CUDA;
+  a.ctx = (void*)ctx;
+  a.ptr = p;
+  *out = p;
   return SG_OK;
 }
 
@@ -943,7 +978,7 @@ extern "C" int sg_replay_noalloc(const sg_job* jobs_dev, uint32_t n, uint64_t bu
   if (n == 0) return SG_OK;
   if (!jobs_dev || !log_dev) return SG_ERR_INVALID;
   void* ws = nullptr;
-  int rc = scratch_address(&ws);
+  int rc = scratch_address((cudaStream_t)stream, &ws);
   if (rc != SG_OK) return rc;
   // the replay kernels initialise every part of the workspace they read, so
   // the previous call's contents need no clearing

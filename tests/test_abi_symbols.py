@@ -96,3 +96,14 @@ def test_binding_constants_match_the_header():
     for name in ("SG_OK", "SG_ERR_DEVICE", "SG_POLICY_PRIO_FIRST_FIT", "SG_DEVERR_ITEM"):
         assert hasattr(abi, name), name
     assert checked >= 20
+
+
+def test_no_alloc_workspace_holds_the_stated_limit():
+    """The fixed array behind sg_replay_noalloc (2048 KiB) holds the workspace
+    of a trace of exactly SG_REPLAY_NOALLOC_MAX_JOBS jobs; a larger trace is
+    refused before any device work."""
+    from paper_1712_04495_b300 import abi
+    lib = abi.lib()
+    n = abi.SG_REPLAY_NOALLOC_MAX_JOBS
+    assert lib.sg_replay_workspace_bytes(n) <= 2048 * 1024
+    assert lib.sg_replay_noalloc(None, n + 1, 1 << 20, 256, 0, 0, 0, None, None, None) == abi.SG_ERR_TOO_LARGE
