@@ -20,8 +20,8 @@ from paper_1712_04495_b300 import tracegen as tg
 
 # ------------------------------------------------------------------- triad
 def triad_inputs(key: int, idx):
-    b = tg.uniform_pm1_f32(tg.sm64_at(tg.stream_key(key, 1), idx))
-    c = tg.uniform_pm1_f32(tg.sm64_at(tg.stream_key(key, 2), idx))
+    b = tg.uniform_stream_f32(tg.stream_key(key, 1), idx)
+    c = tg.uniform_stream_f32(tg.stream_key(key, 2), idx)
     return b, c
 
 
@@ -51,7 +51,7 @@ def spmv_csr(key: int, rows: int, table):
     e = np.arange(ptr[-1], dtype=np.uint64)
     col = tg.spmv_columns(tg.stream_key(key, 2), e, rows)
     val = tg.spmv_values(tg.stream_key(key, 3), e)
-    x = tg.uniform_pm1_f32(tg.sm64_at(tg.stream_key(key, 4), np.arange(rows, dtype=np.uint64)))
+    x = tg.uniform_stream_f32(tg.stream_key(key, 4), np.arange(rows, dtype=np.uint64))
     return ptr, col, val, x
 
 
@@ -80,7 +80,7 @@ def spmv_sampled(key: int, rows: int, table, sample_rows):
         e = np.arange(ptr[r], ptr[r + 1], dtype=np.uint64)
         col = tg.spmv_columns(kc, e, rows)
         val = tg.spmv_values(kv, e).astype(np.float64)
-        x = tg.uniform_pm1_f32(tg.sm64_at(kx, col.astype(np.uint64))).astype(np.float64)
+        x = tg.uniform_stream_f32(kx, col.astype(np.uint64)).astype(np.float64)
         y[t] = float(np.sum(val * x))
         mag[t] = float(np.sum(np.abs(val * x)))
     return y, mag, ptr
@@ -114,7 +114,7 @@ def spmv_sampled_streamed(key: int, rows: int, table, sample_rows, chunk: int = 
         e = np.arange(starts[t], ends[t], dtype=np.uint64)
         col = tg.spmv_columns(kc, e, rows)
         val = tg.spmv_values(kv, e).astype(np.float64)
-        x = tg.uniform_pm1_f32(tg.sm64_at(kx, col.astype(np.uint64))).astype(np.float64)
+        x = tg.uniform_stream_f32(kx, col.astype(np.uint64)).astype(np.float64)
         y[t] = float(np.sum(val * x))
         mag[t] = float(np.sum(np.abs(val * x)))
     return y, mag, starts, ends, base
@@ -125,7 +125,7 @@ def gemm_a(key: int, m: int, k: int, rows=None) -> np.ndarray:
     """A[i, :] as fp64 values of the bf16 inputs (rows defaults to all m)."""
     rows = np.arange(m) if rows is None else np.asarray(rows, dtype=np.int64)
     idx = (rows[:, None].astype(np.uint64) * np.uint64(k) + np.arange(k, dtype=np.uint64)[None, :])
-    u = tg.uniform_pm1_f32(tg.sm64_at(tg.stream_key(key, 1), idx))
+    u = tg.uniform_stream_f32(tg.stream_key(key, 1), idx)
     return tg.bf16_bits_to_f64(tg.bf16_bits_rne(u))
 
 
@@ -133,7 +133,7 @@ def gemm_bt(key: int, n: int, k: int, rows=None) -> np.ndarray:
     """B^T[j, :] (B stored N x K, K contiguous) as fp64 of the bf16 inputs."""
     rows = np.arange(n) if rows is None else np.asarray(rows, dtype=np.int64)
     idx = (rows[:, None].astype(np.uint64) * np.uint64(k) + np.arange(k, dtype=np.uint64)[None, :])
-    u = tg.uniform_pm1_f32(tg.sm64_at(tg.stream_key(key, 2), idx))
+    u = tg.uniform_stream_f32(tg.stream_key(key, 2), idx)
     return tg.bf16_bits_to_f64(tg.bf16_bits_rne(u))
 
 

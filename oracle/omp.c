@@ -42,8 +42,14 @@ static inline uint64_t sm64_at(uint64_t k, uint64_t i) { return mix64(k + (i + 1
 
 uint64_t omp_stream_key(uint64_t job_key, uint64_t stream) { return sm64_at(job_key, stream); }
 
-/* uniform in [-1, 1): the top 24 bits scaled by 2^-23, minus one (exact) */
-static inline float uniform_pm1(uint64_t h) { return (float)((double)(h >> 40) * 0x1p-23 - 1.0); }
+/* element e of a uniform stream with key k, in [-1, 1): 24 bits of the hash
+ * out(k, e / 2) -- bits 40..63 for an even e, bits 8..31 for an odd one --
+ * scaled by 2^-23, minus one (exact) */
+static inline float uniform_at(uint64_t k, uint64_t e) {
+    const uint64_t h = sm64_at(k, e >> 1);
+    const uint64_t b = (e & 1) ? ((h >> 8) & 0xFFFFFFull) : (h >> 40);
+    return (float)((double)b * 0x1p-23 - 1.0);
+}
 
 /* Box-Muller: cos branch for an even element of a pair, sin for an odd one */
 static inline float normal_of(uint64_t h, int odd) {
@@ -73,8 +79,8 @@ void omp_triad(uint64_t key, uint64_t n, float s, float* a) {
     const uint64_t kb = sm64_at(key, 1), kc = sm64_at(key, 2);
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < (int64_t)n; i++) {
-        float b = uniform_pm1(sm64_at(kb, (uint64_t)i));
-        float c = uniform_pm1(sm64_at(kc, (uint64_t)i));
+        float b = uniform_at(kb, (uint64_t)i);
+        float c = uniform_at(kc, (uint64_t)i);
         float p = s * c;          /* first rounding */
         a[i] = b + p;             /* second rounding */
     }
@@ -103,7 +109,7 @@ int64_t omp_spmv(uint64_t key, uint64_t rows, const uint64_t* table, double* y, 
             const uint64_t m = (uint64_t)e >> 1;
             const uint64_t col = column_of(sm64_at(kc, m), odd, rows);
             const double v = (double)normal_of(sm64_at(kv, m), odd);
-            const double x = (double)uniform_pm1(sm64_at(kx, col));
+            const double x = (double)uniform_at(kx, col);
             acc += v * x;
             am += fabs(v * x);
         }
@@ -121,7 +127,7 @@ void omp_gemm_operand(uint64_t key, uint64_t stream, uint64_t rows, uint64_t k, 
     const int64_t count = (int64_t)(rows * k);
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < count; i++) {
-        float f = uniform_pm1(sm64_at(ks, (uint64_t)i));
+        float f = uniform_at(ks, (uint64_t)i);
         uint32_t b;
         memcpy(&b, &f, 4);
         b += 0x7FFFu + ((b >> 16) & 1u);

@@ -448,14 +448,15 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchDev B) {
       const SpmvLayoutHD L = spmv_layout_hd(rows, cap);
       uint64_t* scan = (uint64_t*)(base + L.scan);
       const uint64_t lk = stream_key(job.key, 1);
-      if ((it.phase == 0 && it.chunk < L.nchunks) || it.phase == 2) {
+      uint8_t* lens = (uint8_t*)(base + L.y);   // row lengths, in y until the SpMV writes it
+      if (it.phase == 0 && it.chunk < L.nchunks) {
         if (g.t() < 64) T[gi][g.t()] = B.tables[64ull * job.p2 + g.t()];
         g.sync();
       }
       if (digest) {
         digest_chunk(g, (const uint32_t*)(base + L.y), rows, B.keep + it.job, it.chunk);
       } else if (it.phase == 0) {
-        if (it.chunk < L.nchunks) spmv_chunk_sum(g, T[gi], lk, rows, scan, it.chunk, red[gi]);
+        if (it.chunk < L.nchunks) spmv_chunk_sum(g, T[gi], lk, rows, lens, scan, it.chunk, red[gi]);
         else spmv_fill_chunk(g, (int32_t*)(base + L.col), (float*)(base + L.val), (float*)(base + L.x), cap, rows,
                              stream_key(job.key, 2), stream_key(job.key, 3), stream_key(job.key, 4),
                              it.chunk - L.nchunks);
@@ -463,10 +464,10 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchDev B) {
         spmv_scan(g, scan, L.nchunks, red[gi], &carry[gi]);
       } else if (it.phase == 2) {
         if (L.ptr64)
-          spmv_row_ptr_chunk<SubGroup, int64_t>(g, T[gi], lk, rows, scan, L.nchunks, (int64_t*)(base + L.row_ptr),
+          spmv_row_ptr_chunk<SubGroup, int64_t>(g, lens, rows, scan, L.nchunks, (int64_t*)(base + L.row_ptr),
                                                 cap, B.err, it.chunk, red[gi]);
         else
-          spmv_row_ptr_chunk<SubGroup, int32_t>(g, T[gi], lk, rows, scan, L.nchunks, (int32_t*)(base + L.row_ptr),
+          spmv_row_ptr_chunk<SubGroup, int32_t>(g, lens, rows, scan, L.nchunks, (int32_t*)(base + L.row_ptr),
                                                 cap, B.err, it.chunk, red[gi]);
       } else {
         if (L.ptr64)
@@ -551,7 +552,7 @@ int batch_grid(uint64_t total) {
 int batch_job_ok(const sg_job& jb, const uint64_t* tables_dev) {
   if (jb.kind > SG_KIND_GEMM) return SG_ERR_INVALID;
   if (jb.kind == SG_KIND_GEMM && (jb.p2 == 0 || jb.p2 % 8 || jb.p0 == 0 || jb.p1 == 0)) return SG_ERR_INVALID;
-  if (jb.kind == SG_KIND_SPMV && (!tables_dev || jb.p0 == 0)) return SG_ERR_INVALID;
+  if (jb.kind == SG_KIND_SPMV && (!tables_dev || jb.p0 == 0 || jb.p0 > 0xFFFFFFFFull)) return SG_ERR_INVALID;
   if (jb.kind == SG_KIND_TRIAD && jb.p0 == 0) return SG_ERR_INVALID;
   return SG_OK;
 }

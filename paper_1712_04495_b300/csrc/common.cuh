@@ -28,9 +28,21 @@ __host__ __device__ __forceinline__ uint64_t stream_key(uint64_t k, uint64_t s) 
   return sm64_at(k, s);
 }
 
-// uniform[-1, 1): 24 high bits scaled by 2^-23, minus one; exact in fp32
-__device__ __forceinline__ float uniform_pm1(uint64_t h) {
-  return __fsub_rn(__fmul_rn((float)(uint32_t)(h >> 40), 0x1p-23f), 1.0f);
+// uniform[-1, 1) from 24 random bits: b * 2^-23 - 1, exact in fp32 (the
+// product is exact, so one fused multiply-add rounds like the
+// product-then-difference it stands for)
+__device__ __forceinline__ float uniform_pm1_bits(uint32_t b24) {
+  return __fmaf_rn((float)b24, 0x1p-23f, -1.0f);
+}
+// The two uniforms one hash gives a uniform stream: element 2m takes bits
+// 40..63 of h = out(K, m), element 2m + 1 bits 8..31.
+__device__ __forceinline__ float2 uniform_pair(uint64_t h) {
+  return make_float2(uniform_pm1_bits((uint32_t)(h >> 40)), uniform_pm1_bits((uint32_t)(h >> 8) & 0xFFFFFFu));
+}
+// element e of the uniform stream with key k
+__device__ __forceinline__ float uniform_at(uint64_t k, uint64_t e) {
+  const uint64_t h = sm64_at(k, e >> 1);
+  return uniform_pm1_bits((e & 1) ? ((uint32_t)(h >> 8) & 0xFFFFFFu) : (uint32_t)(h >> 40));
 }
 
 // Two N(0,1) values by Box-Muller on two 24-bit uniforms taken from one
@@ -44,9 +56,16 @@ __device__ __forceinline__ float2 normal_pair(uint64_t h) {
   return make_float2(r * cs, r * sn);
 }
 
-// column index in [0, n) from 32 random bits: multiply-shift
-__device__ __forceinline__ uint32_t column_of32(uint32_t w, uint64_t n) {
-  return (uint32_t)(((uint64_t)w * n) >> 32);
+// column index in [0, n) from 32 random bits: multiply-shift, (w * n) >> 32,
+// which for n < 2^32 is the high word of the 32 x 32-bit product
+__device__ __forceinline__ uint32_t column_of32(uint32_t w, uint32_t n) { return __umulhi(w, n); }
+
+// two fp32 values as a packed bf16 pair (lo in bits 0..15), each rounded to
+// nearest, ties to even, by the hardware conversion
+__device__ __forceinline__ uint32_t bf16x2_rne_bits(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
 }
 
 // bf16 bits of an fp32 value, round to nearest, ties to even (finite input)

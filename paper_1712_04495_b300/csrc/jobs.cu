@@ -66,12 +66,14 @@ __global__ void __launch_bounds__(kChunkThreads, 6) k_spmv(const PtrT* __restric
 
 __global__ void __launch_bounds__(kChunkThreads) k_spmv_chunk_sums(const uint64_t* __restrict__ table,
                                                                    uint64_t len_key, uint64_t rows,
+                                                                   uint8_t* __restrict__ lens,
                                                                    uint64_t* __restrict__ scan, uint64_t nchunks) {
   __shared__ uint64_t T[64];
   __shared__ uint64_t red[kChunkThreads / 32];
   if (threadIdx.x < 64) T[threadIdx.x] = table[threadIdx.x];
   __syncthreads();
-  for (uint64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) spmv_chunk_sum(BlockGroup{}, T, len_key, rows, scan, ch, red);
+  for (uint64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x)
+    spmv_chunk_sum(BlockGroup{}, T, len_key, rows, lens, scan, ch, red);
 }
 
 __global__ void __launch_bounds__(kChunkThreads) k_spmv_scan_chunks(uint64_t* __restrict__ scan, uint64_t n) {
@@ -81,17 +83,13 @@ __global__ void __launch_bounds__(kChunkThreads) k_spmv_scan_chunks(uint64_t* __
 }
 
 template <typename PtrT>
-__global__ void __launch_bounds__(kChunkThreads) k_spmv_row_ptr(const uint64_t* __restrict__ table,
-                                                                uint64_t len_key, uint64_t rows,
+__global__ void __launch_bounds__(kChunkThreads) k_spmv_row_ptr(const uint8_t* __restrict__ lens, uint64_t rows,
                                                                 const uint64_t* __restrict__ scan,
                                                                 uint64_t nchunks, PtrT* __restrict__ row_ptr,
                                                                 uint64_t cap, uint32_t* err) {
-  __shared__ uint64_t T[64];
   __shared__ uint64_t wsum[kChunkThreads / 32];
-  if (threadIdx.x < 64) T[threadIdx.x] = table[threadIdx.x];
-  __syncthreads();
   for (uint64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x)
-    spmv_row_ptr_chunk<BlockGroup, PtrT>(BlockGroup{}, T, len_key, rows, scan, nchunks, row_ptr, cap, err, ch, wsum);
+    spmv_row_ptr_chunk<BlockGroup, PtrT>(BlockGroup{}, lens, rows, scan, nchunks, row_ptr, cap, err, ch, wsum);
 }
 
 __global__ void __launch_bounds__(kChunkThreads) k_spmv_fill(int32_t* __restrict__ col, float* __restrict__ val,
@@ -160,14 +158,15 @@ int launch_gen_spmv(char* base, uint64_t rows, uint64_t nnz, const uint64_t* tab
   uint64_t* scan = (uint64_t*)(base + L.scan);
   uint64_t lk = stream_key(key, 1);
   unsigned nch = (unsigned)L.nchunks;
-  k_spmv_chunk_sums<<<nch, kChunkThreads, 0, st>>>(table, lk, rows, scan, L.nchunks);
+  uint8_t* lens = (uint8_t*)(base + L.y);   // row lengths, in y until the SpMV writes it
+  k_spmv_chunk_sums<<<nch, kChunkThreads, 0, st>>>(table, lk, rows, lens, scan, L.nchunks);
   k_spmv_scan_chunks<<<1, kChunkThreads, 0, st>>>(scan, L.nchunks);
   if (L.ptr64)
-    k_spmv_row_ptr<int64_t><<<nch, kChunkThreads, 0, st>>>(table, lk, rows, scan, L.nchunks,
-                                                      (int64_t*)(base + L.row_ptr), nnz, err);
+    k_spmv_row_ptr<int64_t><<<nch, kChunkThreads, 0, st>>>(lens, rows, scan, L.nchunks,
+                                                           (int64_t*)(base + L.row_ptr), nnz, err);
   else
-    k_spmv_row_ptr<int32_t><<<nch, kChunkThreads, 0, st>>>(table, lk, rows, scan, L.nchunks,
-                                                      (int32_t*)(base + L.row_ptr), nnz, err);
+    k_spmv_row_ptr<int32_t><<<nch, kChunkThreads, 0, st>>>(lens, rows, scan, L.nchunks,
+                                                           (int32_t*)(base + L.row_ptr), nnz, err);
   k_spmv_fill<<<grid_for((nnz > 4 * rows ? nnz : 4 * rows), kFillChunk), kChunkThreads, 0, st>>>(
       (int32_t*)(base + L.col), (float*)(base + L.val), (float*)(base + L.x), scan + L.nchunks, nnz,
       rows, stream_key(key, 2), stream_key(key, 3), stream_key(key, 4));

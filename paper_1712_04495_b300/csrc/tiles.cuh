@@ -102,6 +102,7 @@ __device__ __forceinline__ void triad_chunk(const G& g, float* __restrict__ a, c
   }
 }
 
+// b and c from their uniform streams: one hash per two elements
 template <class G>
 __device__ __forceinline__ void gen_triad_chunk(const G& g, float* __restrict__ b, float* __restrict__ c, uint64_t n,
                                                 uint64_t kb, uint64_t kc, int vec, uint64_t chunk) {
@@ -111,25 +112,23 @@ __device__ __forceinline__ void gen_triad_chunk(const G& g, float* __restrict__ 
 #pragma unroll
     for (int k = 0; k < 4; k++) {
       const uint64_t i = (e0 >> 2) + g.t() + k * kChunkThreads;
-      const uint64_t e = i << 2;
-      float4 vb, vc;
-      vb.x = uniform_pm1(sm64_at(kb, e)); vb.y = uniform_pm1(sm64_at(kb, e + 1));
-      vb.z = uniform_pm1(sm64_at(kb, e + 2)); vb.w = uniform_pm1(sm64_at(kb, e + 3));
-      vc.x = uniform_pm1(sm64_at(kc, e)); vc.y = uniform_pm1(sm64_at(kc, e + 1));
-      vc.z = uniform_pm1(sm64_at(kc, e + 2)); vc.w = uniform_pm1(sm64_at(kc, e + 3));
-      reinterpret_cast<float4*>(b)[i] = vb;
-      reinterpret_cast<float4*>(c)[i] = vc;
+      const uint64_t m = i << 1;   // hashes 2i and 2i + 1 cover elements 4i .. 4i + 3
+      const float2 b0 = uniform_pair(sm64_at(kb, m)), b1 = uniform_pair(sm64_at(kb, m + 1));
+      const float2 c0 = uniform_pair(sm64_at(kc, m)), c1 = uniform_pair(sm64_at(kc, m + 1));
+      reinterpret_cast<float4*>(b)[i] = make_float4(b0.x, b0.y, b1.x, b1.y);
+      reinterpret_cast<float4*>(c)[i] = make_float4(c0.x, c0.y, c1.x, c1.y);
     }
   } else {
     for (uint64_t i = e0 + g.t(); i < e1; i += kChunkThreads) {
-      b[i] = uniform_pm1(sm64_at(kb, i));
-      c[i] = uniform_pm1(sm64_at(kc, i));
+      b[i] = uniform_at(kb, i);
+      c[i] = uniform_at(kc, i);
     }
   }
 }
 
 // ------------------------------------------------------------ bf16 inputs
-// eight bf16 per thread per step (one 16-byte store); `out` 16-byte aligned
+// eight bf16 per thread per step (one 16-byte store, four hashes); `out`
+// 16-byte aligned
 template <class G>
 __device__ __forceinline__ void gen_bf16_chunk(const G& g, uint16_t* __restrict__ out, uint64_t count, uint64_t key,
                                                uint64_t chunk) {
@@ -140,13 +139,12 @@ __device__ __forceinline__ void gen_bf16_chunk(const G& g, uint16_t* __restrict_
       uint32_t w[4];
 #pragma unroll
       for (int k = 0; k < 4; k++) {
-        uint32_t lo = bf16_rne_bits(uniform_pm1(sm64_at(key, e + 2 * k)));
-        uint32_t hi = bf16_rne_bits(uniform_pm1(sm64_at(key, e + 2 * k + 1)));
-        w[k] = lo | (hi << 16);
+        const float2 u = uniform_pair(sm64_at(key, (e >> 1) + k));
+        w[k] = bf16x2_rne_bits(u.x, u.y);
       }
       *reinterpret_cast<uint4*>(out + e) = make_uint4(w[0], w[1], w[2], w[3]);
     } else {
-      for (uint64_t i = e; i < e1; i++) out[i] = (uint16_t)bf16_rne_bits(uniform_pm1(sm64_at(key, i)));
+      for (uint64_t i = e; i < e1; i++) out[i] = (uint16_t)bf16_rne_bits(uniform_at(key, i));
     }
   }
 }
@@ -243,15 +241,30 @@ __device__ __forceinline__ uint64_t block_sum_u64(const G& g, uint64_t v, uint64
   return t;
 }
 
-// sum of the row lengths of scan chunk `chunk` -> scan[chunk]; T in shared memory
+// Row lengths of scan chunk `chunk`: each thread takes 16 consecutive rows,
+// stores their lengths as 16 bytes (a length is at most 64) at lens[first
+// row], and the block's total goes to scan[chunk]. `lens` is the job's y
+// array, free until the SpMV writes y; the row_ptr pass reads the lengths
+// back instead of hashing every row a second time. The last thread of a
+// ragged chunk writes zeros past the last row, inside y (4 bytes per row,
+// rounded up to 256). T in shared memory.
 template <class G>
 __device__ __forceinline__ void spmv_chunk_sum(const G& g, const uint64_t* T, uint64_t len_key, uint64_t rows,
-                                               uint64_t* __restrict__ scan, uint64_t chunk, uint64_t* red) {
-  const uint64_t r0 = chunk * kRowsPerScanChunk;
+                                               uint8_t* __restrict__ lens, uint64_t* __restrict__ scan,
+                                               uint64_t chunk, uint64_t* red) {
+  constexpr int kPer = kRowsPerScanChunk / kChunkThreads;
+  static_assert(kPer == 16, "one 16-byte store of lengths per thread");
+  const uint64_t r0 = chunk * kRowsPerScanChunk + (uint64_t)g.t() * kPer;
   uint64_t sum = 0;
-  for (uint32_t k = g.t(); k < kRowsPerScanChunk; k += kChunkThreads) {
-    uint64_t r = r0 + k;
-    if (r < rows) sum += row_len(T, len_key, r);
+  if (r0 < rows) {
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int k = 0; k < kPer; k++) {
+      const uint32_t l = (r0 + k < rows) ? row_len(T, len_key, r0 + k) : 0u;
+      w[k >> 2] |= l << (8 * (k & 3));
+      sum += l;
+    }
+    *reinterpret_cast<uint4*>(lens + r0) = make_uint4(w[0], w[1], w[2], w[3]);
   }
   sum = block_sum_u64(g, sum, red);
   if (g.t() == 0) scan[chunk] = sum;
@@ -294,19 +307,24 @@ __device__ __forceinline__ void spmv_scan(const G& g, uint64_t* __restrict__ sca
   if (g.t() == 0) scan[n] = *carry;
 }
 
-// row_ptr of the rows of scan chunk `chunk` (16 consecutive rows per thread)
+// row_ptr of the rows of scan chunk `chunk` (16 consecutive rows per
+// thread, their lengths read back from `lens` as one 16-byte load; the
+// row_ptr entries leave as 16-byte stores).
 template <class G, typename PtrT>
-__device__ __forceinline__ void spmv_row_ptr_chunk(const G& g, const uint64_t* T, uint64_t len_key, uint64_t rows,
+__device__ __forceinline__ void spmv_row_ptr_chunk(const G& g, const uint8_t* __restrict__ lens, uint64_t rows,
                                                    const uint64_t* __restrict__ scan, uint64_t nchunks,
                                                    PtrT* __restrict__ row_ptr, uint64_t cap, uint32_t* err,
                                                    uint64_t chunk, uint64_t* wsum) {
   constexpr int kPer = kRowsPerScanChunk / kChunkThreads;
   const uint64_t r0 = chunk * kRowsPerScanChunk + (uint64_t)g.t() * kPer;
+  uint4 q = make_uint4(0u, 0u, 0u, 0u);
+  if (r0 < rows) q = *reinterpret_cast<const uint4*>(lens + r0);
+  const uint32_t qw[4] = {q.x, q.y, q.z, q.w};
   uint32_t len[kPer];
   uint64_t mine = 0;
 #pragma unroll
   for (int k = 0; k < kPer; k++) {
-    len[k] = (r0 + k < rows) ? row_len(T, len_key, r0 + k) : 0u;
+    len[k] = (qw[k >> 2] >> (8 * (k & 3))) & 0xFFu;
     mine += len[k];
   }
   const uint32_t lane = g.t() & 31, w = g.t() >> 5;
@@ -321,10 +339,24 @@ __device__ __forceinline__ void spmv_row_ptr_chunk(const G& g, const uint64_t* T
   uint64_t woff = 0;
   for (uint32_t k = 0; k < w; k++) woff += wsum[k];
   uint64_t pos = scan[chunk] + woff + incl - mine;
+  PtrT v[kPer];
 #pragma unroll
   for (int k = 0; k < kPer; k++) {
-    if (r0 + k < rows) row_ptr[r0 + k] = (PtrT)(pos < cap ? pos : cap);  // clamp keeps reads in bounds
+    v[k] = (PtrT)(pos < cap ? pos : cap);  // clamp keeps reads in bounds
     pos += len[k];
+  }
+  if (r0 + kPer <= rows) {  // row_ptr + r0 is 64-byte aligned: r0 is a multiple of 16
+    constexpr int kVec = 16 / sizeof(PtrT);
+#pragma unroll
+    for (int k = 0; k < kPer; k += kVec) {
+      uint4 u;
+      memcpy(&u, &v[k], 16);
+      *reinterpret_cast<uint4*>(row_ptr + r0 + k) = u;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kPer; k++)
+      if (r0 + k < rows) row_ptr[r0 + k] = v[k];
   }
   if (chunk == 0 && g.t() == 0) {
     uint64_t total = scan[nchunks];
@@ -345,27 +377,33 @@ __device__ __forceinline__ void spmv_fill_chunk(const G& g, int32_t* __restrict_
                                                 uint64_t kc, uint64_t kv, uint64_t kx, uint64_t chunk) {
   const uint64_t e0 = chunk * kFillChunk;
   const uint64_t e1 = e0 + kFillChunk < nnz ? e0 + kFillChunk : nnz;
+  const uint32_t n32 = (uint32_t)rows;   // rows < 2^32 (checked at launch)
   for (uint64_t e = e0 + 4 * g.t(); e < e1; e += 4 * kChunkThreads) {
     if (e + 4 <= e1) {
       const uint64_t m = e >> 1;
       const uint64_t hc0 = sm64_at(kc, m), hc1 = sm64_at(kc, m + 1);
-      const int4 cc = make_int4((int)column_of32((uint32_t)(hc0 >> 32), rows), (int)column_of32((uint32_t)hc0, rows),
-                                (int)column_of32((uint32_t)(hc1 >> 32), rows), (int)column_of32((uint32_t)hc1, rows));
+      const int4 cc = make_int4((int)column_of32((uint32_t)(hc0 >> 32), n32), (int)column_of32((uint32_t)hc0, n32),
+                                (int)column_of32((uint32_t)(hc1 >> 32), n32), (int)column_of32((uint32_t)hc1, n32));
       const float2 v0 = normal_pair(sm64_at(kv, m)), v1 = normal_pair(sm64_at(kv, m + 1));
       *reinterpret_cast<int4*>(col + e) = cc;
       *reinterpret_cast<float4*>(val + e) = make_float4(v0.x, v0.y, v1.x, v1.y);
     } else {
       for (uint64_t i = e; i < e1; i++) {
         const uint64_t hc = sm64_at(kc, i >> 1);
-        col[i] = (int32_t)column_of32((i & 1) ? (uint32_t)hc : (uint32_t)(hc >> 32), rows);
+        col[i] = (int32_t)column_of32((i & 1) ? (uint32_t)hc : (uint32_t)(hc >> 32), n32);
         const float2 v = normal_pair(sm64_at(kv, i >> 1));
         val[i] = (i & 1) ? v.y : v.x;
       }
     }
   }
+  // x: two rows per hash, one 8-byte store (x0 is even, x 8-byte aligned)
   const uint64_t x0 = chunk * (kFillChunk / 4);
   const uint64_t x1 = x0 + kFillChunk / 4 < rows ? x0 + kFillChunk / 4 : rows;
-  for (uint64_t r = x0 + g.t(); r < x1; r += kChunkThreads) x[r] = uniform_pm1(sm64_at(kx, r));
+  for (uint64_t r = x0 + 2 * g.t(); r < x1; r += 2 * kChunkThreads) {
+    const float2 u = uniform_pair(sm64_at(kx, r >> 1));
+    if (r + 1 < x1) *reinterpret_cast<float2*>(x + r) = u;
+    else x[r] = u.x;
+  }
 }
 
 __device__ __forceinline__ uint64_t spmv_fill_chunks(uint64_t nnz_cap, uint64_t rows) {

@@ -18,8 +18,12 @@ A job of trace seed ``S`` and index ``j`` has data key ``K_j = out(S, j)``;
 its data stream ``s`` has key ``K_{j,s} = out(K_j, s)``; element ``i`` of that
 stream is drawn from ``h = out(K_{j,s}, i)``.
 
-  uniform[-1, 1)  u = (h >> 40) * 2^-23 - 1                 (exact in fp32)
   row length      L = #{k : T[k] <= (h >> 32)}, T the Poisson CDF table below
+
+Uniform streams give two elements per hash, h = out(K, m) for elements
+e = 2m, 2m + 1:
+  uniform[-1, 1)  u = b * 2^-23 - 1 (exact in fp32), b = h >> 40 for e even,
+                  b = (h >> 8) & 0xFFFFFF for e odd (24 bits each)
   bf16            round-to-nearest-even of the fp32 uniform
 
 SpMV non-zeros come in pairs (e = 2m, 2m + 1), one hash per pair and per
@@ -30,9 +34,10 @@ quantity, h = out(K, m):
                   r = sqrt(-2 ln u1); v = r cos(2 pi u2) for e even, r sin(2 pi u2)
                   for e odd (Box-Muller's two independent normals)
 
-Streams: triad b=1, c=2; GEMM A=1 (index i*K+k), B^T=2 (index j*K+k);
-SpMV row lengths=1 (index row), columns=2 (index e // 2), values=3 (index
-e // 2), x=4 (index col).
+Streams: triad b=1, c=2 (element i); GEMM A=1 (element i*K+k), B^T=2
+(element j*K+k); SpMV row lengths=1 (hash index row), columns=2 (hash
+index e // 2), values=3 (hash index e // 2), x=4 (element col). The
+uniform streams (b, c, A, B^T, x) are addressed by element, two per hash.
 
 Job record (``JOB_DTYPE``, 64 bytes, the C struct ``sg_job``): arrival,
 declared bytes, declared duration (replay clock), timeout, data key, kind
@@ -103,9 +108,17 @@ def job_keys(seed: int, n: int) -> np.ndarray:
 
 
 # ------------------------------------------------------------ element values
-def uniform_pm1_f32(h) -> np.ndarray:
+def uniform_pm1_f32(h, odd=False) -> np.ndarray:
+    """The uniform of an even (bits 40..63 of h) or odd (bits 8..31) element."""
     h = np.asarray(h, dtype=_U64)
-    return ((h >> _U64(40)).astype(np.float64) * 2.0 ** -23 - 1.0).astype(np.float32)
+    b = np.where(np.asarray(odd, bool), (h >> _U64(8)) & _U64(0xFFFFFF), h >> _U64(40))
+    return (b.astype(np.float64) * 2.0 ** -23 - 1.0).astype(np.float32)
+
+
+def uniform_stream_f32(key: int, e) -> np.ndarray:
+    """Elements e of the uniform stream with key ``key`` (two per hash)."""
+    e = np.asarray(e, dtype=_U64)
+    return uniform_pm1_f32(sm64_at(key, e >> _U64(1)), (e & _U64(1)) == _U64(1))
 
 
 def normal_pair_f32(h, odd) -> np.ndarray:

@@ -42,6 +42,37 @@ def test_uniform_exact_and_range():
     assert np.all(k == np.floor(k))
     assert np.array_equal(k.astype(np.uint64), (h >> np.uint64(40)))
     assert abs(float(u.mean())) < 0.01
+    # odd elements: bits 8..31 of the same hash
+    v = tg.uniform_pm1_f32(h, odd=True)
+    kv = (v.astype(np.float64) + 1.0) * 2.0 ** 23
+    assert np.all(kv == np.floor(kv)) and v.min() >= -1.0 and v.max() < 1.0
+    assert np.array_equal(kv.astype(np.uint64), (h >> np.uint64(8)) & np.uint64(0xFFFFFF))
+    assert abs(float(v.mean())) < 0.01
+    # the two halves of one hash are uncorrelated
+    assert abs(float(np.corrcoef(u, v)[0, 1])) < 0.01
+
+
+def test_uniform_stream_two_elements_per_hash():
+    """Element e of a uniform stream, from a scalar restatement: the SplitMix64
+    output e // 2, its bits 40..63 (e even) or 8..31 (e odd), times 2^-23, minus 1."""
+    M = (1 << 64) - 1
+    key = 0x1234_5678_9ABC_DEF0
+
+    def out(k, i):
+        z = (k + (i + 1) * tg.GAMMA) & M
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+        return z ^ (z >> 31)
+
+    e = np.array([0, 1, 2, 3, 4, 5, 1000, 1001, (1 << 33) + 6, (1 << 33) + 7], dtype=np.uint64)
+    got = tg.uniform_stream_f32(key, e)
+    for ei, g in zip(e.tolist(), got.tolist()):
+        h = out(key, ei // 2)
+        b = (h >> 8) & 0xFFFFFF if ei % 2 else h >> 40
+        assert g == np.float32(b * 2.0 ** -23 - 1.0), ei
+    u = tg.uniform_stream_f32(key, np.arange(200000, dtype=np.uint64))
+    assert abs(float(u.mean())) < 0.01 and abs(float(u.var()) - 1.0 / 3.0) < 0.01
+    assert abs(float(np.corrcoef(u[0::2], u[1::2])[0, 1])) < 0.01
 
 
 def test_bf16_rne_matches_torch():
