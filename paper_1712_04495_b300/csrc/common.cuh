@@ -46,14 +46,54 @@ __device__ __forceinline__ float uniform_at(uint64_t k, uint64_t e) {
 }
 
 // Two N(0,1) values by Box-Muller on two 24-bit uniforms taken from one
-// hash: r cos(2 pi u2) (even element of a pair) and r sin(2 pi u2) (odd).
+// hash: r cos(2 pi u2) (even element of a pair) and r sin(2 pi u2) (odd),
+// u1 = (b1 + 1) 2^-24 in (0, 1], u2 = b2 2^-24 in [0, 1), r = sqrt(-2 ln u1).
+// Each value is within a few units in the last place of the exact one (the
+// oracle's fp64 Box-Muller rounded once), in relative terms even near zero:
+//  - ln u1 = k ln 2 + ln m, m in [sqrt(1/2), sqrt(2)] from the exact fp32
+//    value of b1 + 1; ln m = 2 atanh(s), s = (m - 1) / (m + 1), by its odd
+//    series to s^9 (|s| <= 0.172, next term below 2^-28 relative); ln 2 in
+//    two parts (Cody and Waite) so that k ln 2 has no rounding for |k| <= 24;
+//  - 2 pi u2 = (q + x) pi / 2 with q the nearest integer to 4 u2 and
+//    x in [-1/2, 1/2], both exact from the bits of b2; sin and cos of
+//    x pi / 2 by their Taylor series to the x^9 and x^10 terms (next terms
+//    below 2^-28 on |x pi / 2| <= pi / 4), then the quadrant q.
 __device__ __forceinline__ float2 normal_pair(uint64_t h) {
-  float u1 = (float)((uint32_t)(h >> 40) + 1u) * 0x1p-24f;            // (0, 1]
-  float u2 = (float)((uint32_t)(h >> 16) & 0xFFFFFFu) * 0x1p-24f;     // [0, 1)
-  float r = sqrtf(-2.0f * logf(u1));
-  float sn, cs;
-  sincospif(2.0f * u2, &sn, &cs);
-  return make_float2(r * cs, r * sn);
+  // r
+  const float v = (float)((uint32_t)(h >> 40) + 1u);   // b1 + 1 in [1, 2^24], exact
+  const uint32_t vb = __float_as_uint(v);
+  const uint32_t mb = vb & 0x7FFFFFu;
+  const bool big = mb > 0x3504F3u;                        // mantissa above sqrt(2)
+  const float m = __uint_as_float(mb | (big ? 0x3F000000u : 0x3F800000u));
+  const float k = (float)((int)(vb >> 23) - 127 + (big ? 1 : 0) - 24);
+  const float sq = __fdividef(m - 1.0f, m + 1.0f);
+  const float s2 = sq * sq;
+  float pl = fmaf(s2, 0x1.c71c72p-3f, 0x1.24924ap-2f);   // 2/9, 2/7
+  pl = fmaf(s2, pl, 0x1.99999ap-2f);                     // 2/5
+  pl = fmaf(s2, pl, 0x1.555556p-1f);                     // 2/3
+  pl = fmaf(s2, pl, 2.0f);
+  const float lnu = fmaf(k, 0x1.62e4p-1f, fmaf(k, 0x1.7f7d1cp-20f, sq * pl));   // ln 2 = hi + lo
+  const float L = -2.0f * lnu;
+  const float r = L > 0.0f ? L * rsqrtf(L) : 0.0f;
+  // sin and cos of 2 pi u2
+  const int32_t b2 = (int32_t)((h >> 16) & 0xFFFFFFu);
+  const int32_t q = (b2 + (1 << 21)) >> 22;               // 0..4
+  const float x = (float)(b2 - (q << 22)) * 0x1p-22f;     // [-1/2, 1/2)
+  const float x2 = x * x;
+  float ps = fmaf(x2, 0x1.507834p-13f, -0x1.32d2ccp-8f);  // (pi/2)^9/9!, -(pi/2)^7/7!
+  ps = fmaf(x2, ps, 0x1.466bc6p-4f);                      // (pi/2)^5/5!
+  ps = fmaf(x2, ps, -0x1.4abbcep-1f);                     // -(pi/2)^3/3!
+  ps = fmaf(x2, ps, 0x1.921fb6p+0f);                      // pi/2
+  const float sn = x * ps;
+  float pc = fmaf(x2, -0x1.a6d1f2p-16f, 0x1.e1f506p-11f); // -(pi/2)^10/10!, (pi/2)^8/8!
+  pc = fmaf(x2, pc, -0x1.55d3c8p-6f);                     // -(pi/2)^6/6!
+  pc = fmaf(x2, pc, 0x1.03c1f0p-2f);                      // (pi/2)^4/4!
+  pc = fmaf(x2, pc, -0x1.3bd3ccp+0f);                     // -(pi/2)^2/2!
+  const float cs = fmaf(x2, pc, 1.0f);
+  // quadrant: (sin, cos) of (q + x) pi/2
+  const bool odd = q & 1, neg_s = q & 2, neg_c = (q + 1) & 2;
+  const float sv = odd ? cs : sn, cv = odd ? sn : cs;
+  return make_float2(r * (neg_c ? -cv : cv), r * (neg_s ? -sv : sv));
 }
 
 // column index in [0, n) from 32 random bits: multiply-shift, (w * n) >> 32,
