@@ -125,7 +125,7 @@ def gemm_a(key: int, m: int, k: int, rows=None) -> np.ndarray:
     """A[i, :] as fp64 values of the bf16 inputs (rows defaults to all m)."""
     rows = np.arange(m) if rows is None else np.asarray(rows, dtype=np.int64)
     idx = (rows[:, None].astype(np.uint64) * np.uint64(k) + np.arange(k, dtype=np.uint64)[None, :])
-    u = tg.uniform_stream_f32(tg.stream_key(key, 1), idx)
+    u = tg.bf16_stream_f32(tg.stream_key(key, 1), idx)
     return tg.bf16_bits_to_f64(tg.bf16_bits_rne(u))
 
 
@@ -133,7 +133,7 @@ def gemm_bt(key: int, n: int, k: int, rows=None) -> np.ndarray:
     """B^T[j, :] (B stored N x K, K contiguous) as fp64 of the bf16 inputs."""
     rows = np.arange(n) if rows is None else np.asarray(rows, dtype=np.int64)
     idx = (rows[:, None].astype(np.uint64) * np.uint64(k) + np.arange(k, dtype=np.uint64)[None, :])
-    u = tg.uniform_stream_f32(tg.stream_key(key, 2), idx)
+    u = tg.bf16_stream_f32(tg.stream_key(key, 2), idx)
     return tg.bf16_bits_to_f64(tg.bf16_bits_rne(u))
 
 

@@ -121,13 +121,16 @@ int64_t omp_spmv(uint64_t key, uint64_t rows, const uint64_t* table, double* y, 
 
 /* rows x k matrix of a GEMM operand (stream 1 = A, index i*k + j; stream
  * 2 = B^T) as fp64 values of the bf16-rounded (nearest, ties to even)
- * uniforms. */
+ * uniforms. Element e of a bf16 stream: 16 bits of the hash out(k, e / 4),
+ * bits 16 (e mod 4) and up, scaled by 2^-15, minus one (exact). */
 void omp_gemm_operand(uint64_t key, uint64_t stream, uint64_t rows, uint64_t k, double* out) {
     const uint64_t ks = sm64_at(key, stream);
     const int64_t count = (int64_t)(rows * k);
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < count; i++) {
-        float f = uniform_at(ks, (uint64_t)i);
+        const uint64_t h = sm64_at(ks, (uint64_t)i >> 2);
+        const uint64_t b16 = (h >> (16 * ((uint64_t)i & 3))) & 0xFFFFull;
+        float f = (float)((double)b16 * 0x1p-15 - 1.0);
         uint32_t b;
         memcpy(&b, &f, 4);
         b += 0x7FFFu + ((b >> 16) & 1u);

@@ -100,6 +100,13 @@ __device__ __forceinline__ float2 normal_pair(uint64_t h) {
 // which for n < 2^32 is the high word of the 32 x 32-bit product
 __device__ __forceinline__ uint32_t column_of32(uint32_t w, uint32_t n) { return __umulhi(w, n); }
 
+// The uniform of a 16-bit field b of a bf16 stream, b * 2^-15 - 1 (exact in
+// fp32): 1 + b 2^-16 is built in the mantissa of a float in [1, 2), and
+// 2 (1 + b 2^-16) - 3 is exact.
+__device__ __forceinline__ float uniform16(uint32_t b16) {
+  return __fmaf_rn(__uint_as_float(0x3F800000u | (b16 << 7)), 2.0f, -3.0f);
+}
+
 // two fp32 values as a packed bf16 pair (lo in bits 0..15), each rounded to
 // nearest, ties to even, by the hardware conversion
 __device__ __forceinline__ uint32_t bf16x2_rne_bits(float lo, float hi) {

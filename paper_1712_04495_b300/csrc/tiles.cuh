@@ -127,8 +127,11 @@ __device__ __forceinline__ void gen_triad_chunk(const G& g, float* __restrict__ 
 }
 
 // ------------------------------------------------------------ bf16 inputs
-// eight bf16 per thread per step (one 16-byte store, four hashes); `out`
-// 16-byte aligned
+// Element e of a bf16 stream: bits 16 (e mod 4) .. 16 (e mod 4) + 15 of
+// out(key, e / 4) as a uniform, rounded to bf16. Eight per thread per step
+// (two hashes, one 16-byte store); `out` 16-byte aligned.
+__device__ __forceinline__ uint32_t bf16_field(uint64_t h, int j) { return (uint32_t)(h >> (16 * j)) & 0xFFFFu; }
+
 template <class G>
 __device__ __forceinline__ void gen_bf16_chunk(const G& g, uint16_t* __restrict__ out, uint64_t count, uint64_t key,
                                                uint64_t chunk) {
@@ -136,15 +139,15 @@ __device__ __forceinline__ void gen_bf16_chunk(const G& g, uint16_t* __restrict_
   const uint64_t e1 = e0 + kBf16Chunk < count ? e0 + kBf16Chunk : count;
   for (uint64_t e = e0 + 8 * g.t(); e < e1; e += 8 * kChunkThreads) {
     if (e + 8 <= e1) {
-      uint32_t w[4];
-#pragma unroll
-      for (int k = 0; k < 4; k++) {
-        const float2 u = uniform_pair(sm64_at(key, (e >> 1) + k));
-        w[k] = bf16x2_rne_bits(u.x, u.y);
-      }
-      *reinterpret_cast<uint4*>(out + e) = make_uint4(w[0], w[1], w[2], w[3]);
+      const uint64_t h0 = sm64_at(key, e >> 2), h1 = sm64_at(key, (e >> 2) + 1);
+      const uint4 w = make_uint4(bf16x2_rne_bits(uniform16(bf16_field(h0, 0)), uniform16(bf16_field(h0, 1))),
+                                 bf16x2_rne_bits(uniform16(bf16_field(h0, 2)), uniform16(bf16_field(h0, 3))),
+                                 bf16x2_rne_bits(uniform16(bf16_field(h1, 0)), uniform16(bf16_field(h1, 1))),
+                                 bf16x2_rne_bits(uniform16(bf16_field(h1, 2)), uniform16(bf16_field(h1, 3))));
+      *reinterpret_cast<uint4*>(out + e) = w;
     } else {
-      for (uint64_t i = e; i < e1; i++) out[i] = (uint16_t)bf16_rne_bits(uniform_at(key, i));
+      for (uint64_t i = e; i < e1; i++)
+        out[i] = (uint16_t)bf16_rne_bits(uniform16(bf16_field(sm64_at(key, i >> 2), (int)(i & 3))));
     }
   }
 }

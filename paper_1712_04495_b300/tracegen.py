@@ -24,7 +24,10 @@ Uniform streams give two elements per hash, h = out(K, m) for elements
 e = 2m, 2m + 1:
   uniform[-1, 1)  u = b * 2^-23 - 1 (exact in fp32), b = h >> 40 for e even,
                   b = (h >> 8) & 0xFFFFFF for e odd (24 bits each)
-  bf16            round-to-nearest-even of the fp32 uniform
+bf16 streams (the GEMM operands) give four elements per hash, h = out(K, m)
+for e = 4m + j, j = 0..3, 16 bits each (a bf16 keeps 8 significant bits):
+  bf16 uniform    u = b * 2^-15 - 1 (exact in fp32), b = (h >> 16 j) & 0xFFFF,
+                  then rounded to nearest, ties to even, to bf16
 
 SpMV non-zeros come in pairs (e = 2m, 2m + 1), one hash per pair and per
 quantity, h = out(K, m):
@@ -37,7 +40,8 @@ quantity, h = out(K, m):
 Streams: triad b=1, c=2 (element i); GEMM A=1 (element i*K+k), B^T=2
 (element j*K+k); SpMV row lengths=1 (hash index row), columns=2 (hash
 index e // 2), values=3 (hash index e // 2), x=4 (element col). The
-uniform streams (b, c, A, B^T, x) are addressed by element, two per hash.
+uniform streams (b, c, x) are addressed by element, two per hash, and the
+bf16 streams (A, B^T) by element, four per hash.
 
 Job record (``JOB_DTYPE``, 64 bytes, the C struct ``sg_job``): arrival,
 declared bytes, declared duration (replay clock), timeout, data key, kind
@@ -147,6 +151,15 @@ def spmv_columns(col_key: int, e, n: int) -> np.ndarray:
 def spmv_values(val_key: int, e) -> np.ndarray:
     e = np.asarray(e, dtype=_U64)
     return normal_pair_f32(sm64_at(val_key, e >> _U64(1)), (e & _U64(1)) == _U64(1))
+
+
+def bf16_stream_f32(key: int, e) -> np.ndarray:
+    """Elements e of the bf16 stream with key ``key`` as the fp32 uniforms
+    they round from (four per hash, 16 bits each)."""
+    e = np.asarray(e, dtype=_U64)
+    h = sm64_at(key, e >> _U64(2))
+    b = (h >> (_U64(16) * (e & _U64(3)))) & _U64(0xFFFF)
+    return (b.astype(np.float64) * 2.0 ** -15 - 1.0).astype(np.float32)
 
 
 def bf16_bits_rne(x_f32) -> np.ndarray:

@@ -131,7 +131,7 @@ def test_gemm_matches_fp64(M, N, Kd):
     A, Bt, C = _gemm(M, N, Kd, key)
     # the inputs are the oracle's bf16 values
     ga = A.cpu().numpy().view(np.uint16)
-    ra = tg.bf16_bits_rne(tg.uniform_stream_f32(tg.stream_key(key, 1), np.arange(M * Kd)))
+    ra = tg.bf16_bits_rne(tg.bf16_stream_f32(tg.stream_key(key, 1), np.arange(M * Kd)))
     assert np.array_equal(ga, ra)
     ref = K.gemm(key, M, N, Kd)
     got = C.cpu().numpy().astype(np.float64)

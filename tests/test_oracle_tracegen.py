@@ -75,6 +75,32 @@ def test_uniform_stream_two_elements_per_hash():
     assert abs(float(np.corrcoef(u[0::2], u[1::2])[0, 1])) < 0.01
 
 
+def test_bf16_stream_four_elements_per_hash():
+    """Element e of a bf16 stream, from a scalar restatement: SplitMix64 output
+    e // 4, its 16-bit field number e % 4 (from the low end), times 2^-15, minus 1."""
+    M = (1 << 64) - 1
+    key = 0x0F1E_2D3C_4B5A_6978
+
+    def out(k, i):
+        z = (k + (i + 1) * tg.GAMMA) & M
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+        return z ^ (z >> 31)
+
+    e = np.array([0, 1, 2, 3, 4, 7, 4001, 4002, (1 << 34) + 5], dtype=np.uint64)
+    got = tg.bf16_stream_f32(key, e)
+    for ei, g in zip(e.tolist(), got.tolist()):
+        b = (out(key, ei // 4) >> (16 * (ei % 4))) & 0xFFFF
+        assert g == np.float32(b * 2.0 ** -15 - 1.0), ei
+    u = tg.bf16_stream_f32(key, np.arange(400000, dtype=np.uint64))
+    assert u.min() >= -1.0 and u.max() < 1.0
+    assert abs(float(u.mean())) < 0.01 and abs(float(u.var()) - 1.0 / 3.0) < 0.01
+    for j in range(1, 4):   # the fields of one hash are uncorrelated
+        assert abs(float(np.corrcoef(u[0::4], u[j::4])[0, 1])) < 0.01
+    # and the bf16 values carry the whole 16-bit grid: 2^16 distinct uniforms
+    assert len(np.unique(tg.bf16_stream_f32(key, np.arange(1 << 20, dtype=np.uint64)))) > 60000
+
+
 def test_bf16_rne_matches_torch():
     rng = np.random.default_rng(1)
     x = rng.standard_normal(200000).astype(np.float32)
