@@ -334,6 +334,20 @@ def kernel_roofline(torch, abi, peaks):
     ms = e0.elapsed_time(e1) / reps
     alg = 4 * (rows + 1) + 8 * nnz + 8 * rows
     gbs = alg / (ms * 1e-3) / 1e9
+    # the ceiling that binds it: x[col] gathers alone over the same columns and
+    # x (sg_gather_sum, a measurement kernel), timed the same way
+    gout = torch.empty((nnz + 1023) // 1024, dtype=torch.float32, device="cuda")
+    gargs = (p + lay["col"], p + lay["x"], nnz, gout.data_ptr(), s.cuda_stream)
+    for _ in range(3):
+        abi.sg_gather_sum(*gargs)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(reps):
+        abi.sg_gather_sum(*gargs)
+    e1.record(s)
+    torch.cuda.synchronize()
+    g_ms = e0.elapsed_time(e1) / reps
+    del gout
     out["spmv"] = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                    "frac": gbs / peaks["hbm_gbs"], "traffic": profiled_traffic("spmv_csr_1e7rows_poisson16"),
                    "ms": ms,
@@ -343,7 +357,11 @@ def kernel_roofline(torch, abi, peaks):
                               "L1/L2 sector per 4-byte value (l1tex__t_sector_hit_rate 6.7%); the kernel runs at "
                               "the L1/L2 sector rate of random gathers, with HBM traffic equal to the "
                               "algorithmic bytes",
-                   "gathers_per_s": nnz / (ms * 1e-3)}
+                   "gathers_per_s": nnz / (ms * 1e-3),
+                   "gather_ceiling": {"gathers_per_s": nnz / (g_ms * 1e-3), "ms": g_ms,
+                                      "kernel": "sg_gather_sum: x[col] alone over the SpMV's own columns "
+                                                "(4 per thread from one 128-bit column load, 8 blocks per SM)",
+                                      "spmv_frac": g_ms / ms}}
     # the input generators, alone at the same sizes (instruction-issue and ALU bound)
     tab_ptr = tab.data_ptr()
     del base
@@ -1096,9 +1114,11 @@ def main():
         extra["roofline"]["peak_source"] = peaks["source"] + " (copy bandwidth, kernel timed alone)"
         extra["roofline"]["target"] = kr["spmv"]["target"]
         extra["roofline"]["target_met"] = kr["spmv"]["target_met"]
+        extra["roofline"]["gather_ceiling"] = kr["spmv"]["gather_ceiling"]
         extra["roofline"]["note"] = ("below the 0.70 target: bound by random x gathers (L1/L2 sector rate), not "
-                                     "by HBM; HBM traffic equals the algorithmic bytes; kernels.gemm has the "
-                                     "tcgen05 GEMM")
+                                     "by HBM; HBM traffic equals the algorithmic bytes; gather_ceiling is the "
+                                     "same gathers alone, measured in this run (spmv_frac = the SpMV's fraction "
+                                     "of that rate); kernels.gemm has the tcgen05 GEMM")
         if not args.no_cpu_baseline:
             sample = stratified_samples(trace, 2)[0]
             d, e = oracle_sample(trace, sample)

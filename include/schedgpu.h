@@ -540,7 +540,9 @@ const char* sg_strerror(int code);
 int sg_triad(float* a, const float* b, const float* c, float s, uint64_t n, void* stream);
 
 /* Triad inputs of a job with data key `key`: b = U(stream 1), c = U(stream 2)
- * where U is uniform[-1,1) from SplitMix64 (tracegen's element generator). */
+ * where U is uniform[-1,1) from SplitMix64, two elements per output: element
+ * 2m from bits 40..63 of output m, element 2m + 1 from bits 8..31
+ * (tracegen's element generator). */
 int sg_gen_triad(float* b, float* c, uint64_t n, uint64_t key, void* stream);
 
 /* FP32 CSR SpMV y = A x. row_ptr: rows+1 entries, int32 (ptr64 = 0) or
@@ -597,9 +599,21 @@ int sg_autotune_gemm(const uint32_t* shapes, uint32_t n_shapes, void* scratch, u
 /* Forget every tuned shape. */
 int sg_autotune_clear(void);
 
-/* GEMM inputs: A[i,k] = bf16(U(stream 1, i*K+k)), Bt[j,k] = bf16(U(stream 2, j*K+k)). */
+/* GEMM inputs: A[i,k] = bf16(V(stream 1, i*K+k)), Bt[j,k] = bf16(V(stream 2, j*K+k)),
+ * V the 16-bit uniform b * 2^-15 - 1 with b bits 16 (e mod 4) .. +15 of
+ * SplitMix64 output e / 4 (four elements per output), rounded to nearest
+ * even. */
 int sg_gen_gemm(uint16_t* A, uint16_t* Bt, uint32_t M, uint32_t N, uint32_t K, uint64_t key,
                 void* stream);
+
+/* Measurement kernel, not a step of the method (the paper has no
+ * counterpart): it times the random gathers x[col[i]] that bound the CSR
+ * SpMV job kernel, on the SpMV's own columns. out_dev[c] = sum of
+ * x[col[i]] over i in [1024 c, 1024 (c + 1)) for the ceil(n / 1024) chunks
+ * c; col (int32, n entries, 16-byte aligned, every entry a valid index of
+ * x), x (fp32) and out_dev are device arrays owned by the caller.
+ * SG_ERR_INVALID for a null or misaligned col, a null x or out_dev. */
+int sg_gather_sum(const int32_t* col, const float* x, uint64_t n, float* out_dev, void* stream);
 
 /* Order-independent 64-bit digest of `words` 32-bit words at dev_ptr:
  * sum over i of mix64((i << 32) | word_i), modulo 2^64, added into

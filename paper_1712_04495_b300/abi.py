@@ -143,6 +143,7 @@ _SIGS = {
     "sg_autotune_clear": ([], ctypes.c_int),
     "sg_gen_gemm": ([_P, _P, _U32, _U32, _U32, _U64, _P], ctypes.c_int),
     "sg_digest": ([_P, _U64, _P, _P], ctypes.c_int),
+    "sg_gather_sum": ([_P, _P, _U64, _P, _P], ctypes.c_int),
     "sg_cancel": ([_P, _U32, _P], ctypes.c_int),
     "sg_poll_grants": ([_P, _P, _P, _U32, _P], ctypes.c_int),
     "sg_server_start": ([_P, ctypes.c_char_p, _P], ctypes.c_int),
@@ -510,6 +511,10 @@ def sg_gen_gemm(A, Bt, M: int, N: int, K: int, key: int, stream: int = 0) -> int
 
 def sg_digest(ptr, words: int, out_ptr, stream: int = 0) -> int:
     return lib().sg_digest(ptr, words, out_ptr, stream)
+
+
+def sg_gather_sum(col, x, n: int, out_ptr, stream: int = 0) -> int:
+    return lib().sg_gather_sum(col, x, n, out_ptr, stream)
 
 
 # ------------------------------------------------ shared memory (no server)

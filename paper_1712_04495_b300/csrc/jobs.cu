@@ -108,6 +108,40 @@ __global__ void __launch_bounds__(kChunkThreads) k_gen_bf16(uint16_t* __restrict
   for (uint64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) gen_bf16_chunk(BlockGroup{}, out, count, key, ch);
 }
 
+// Measurement kernel, not a step of a job: the random-gather rate that
+// bounds the CSR SpMV. Sums x[col[i]] over chunks of kGatherChunk indices,
+// one float per chunk (so the gathers are not dropped). Each thread loads four
+// columns as one 16-byte vector, then gathers them; with 32 registers, eight
+// blocks fill an SM. Of the shapes measured on a B300 (4 to 32 gathers per
+// thread, 128 to 1024 threads, 1 to 8 blocks per SM, persistent or not) this
+// one sustained the most gathers per second.
+constexpr uint64_t kGatherChunk = 4 * kChunkThreads;
+__global__ void __launch_bounds__(kChunkThreads, 8) k_gather_sum(const int32_t* __restrict__ col,
+                                                                 const float* __restrict__ x, uint64_t n,
+                                                                 float* __restrict__ out) {
+  __shared__ float wsum[kChunkThreads / 32];
+  const uint64_t nch = (n + kGatherChunk - 1) / kGatherChunk;
+  for (uint64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+    const uint64_t e0 = ch * kGatherChunk + 4 * (uint64_t)threadIdx.x;
+    float acc = 0.f;
+    if (e0 + 4 <= n) {
+      const int4 c = __ldcs(reinterpret_cast<const int4*>(col + e0));
+      acc = __ldg(x + c.x) + __ldg(x + c.y) + __ldg(x + c.z) + __ldg(x + c.w);
+    } else {
+      for (uint64_t e = e0; e < n; e++) acc += __ldg(x + col[e]);
+    }
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(SG_FULL, acc, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float t = 0.f;
+      for (int w = 0; w < kChunkThreads / 32; w++) t += wsum[w];
+      out[ch] = t;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kChunkThreads) k_digest(const uint32_t* __restrict__ w, uint64_t n,
                                                           uint64_t* out, RelHook hook) {
   const uint64_t nch = (n + kDigestChunk - 1) / kDigestChunk;
@@ -303,6 +337,13 @@ extern "C" int sg_gen_gemm(uint16_t* A, uint16_t* Bt, uint32_t M, uint32_t N, ui
   int rc = launch_gen_bf16(A, (uint64_t)M * K, stream_key(key, 1), (cudaStream_t)stream);
   if (rc == SG_OK) rc = launch_gen_bf16(Bt, (uint64_t)N * K, stream_key(key, 2), (cudaStream_t)stream);
   return rc;
+}
+
+extern "C" int sg_gather_sum(const int32_t* col, const float* x, uint64_t n, float* out_dev, void* stream) {
+  if (n == 0) return SG_OK;
+  if (!col || !x || !out_dev || ((uintptr_t)col & 15u)) return SG_ERR_INVALID;
+  k_gather_sum<<<grid_for(n, kGatherChunk), kChunkThreads, 0, (cudaStream_t)stream>>>(col, x, n, out_dev);
+  return cudaPeekAtLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
 }
 
 extern "C" int sg_digest(const void* dev_ptr, uint64_t words, uint64_t* out_dev, void* stream) {

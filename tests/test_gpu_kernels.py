@@ -72,7 +72,7 @@ def _spmv_case(rows, lam, key):
     return raw, lay, ptr_t, table
 
 
-@pytest.mark.parametrize("rows,lam", [(1, 16.0), (7, 16.0), (1000, 8.0), (100003, 16.0)])
+@pytest.mark.parametrize("rows,lam", [(1, 16.0), (7, 16.0), (1000, 8.0), (100003, 16.0), (1000003, 16.0)])
 def test_spmv_generator_and_product(rows, lam):
     key = 991 + rows
     raw, lay, ptr_t, table = _spmv_case(rows, lam, key)
@@ -105,6 +105,25 @@ def test_spmv_full_size_sampled():
     assert np.array_equal(g_ptr, ptr)
     gy = raw[lay["y"]:].view(np.float32)[sample].astype(np.float64)
     assert np.all(np.abs(gy - y) <= 1e-5 * mag + 1e-30)
+
+
+@pytest.mark.parametrize("n", [1, 3, 4, 1024, 1025, 100003])
+def test_gather_sum_matches_numpy(n):
+    """The gather-rate measurement kernel sums x[col] per chunk of 1024 indices."""
+    abi = _abi()
+    rng = np.random.default_rng(n)
+    rows = 5000
+    col = rng.integers(0, rows, n).astype(np.int32)
+    x = rng.uniform(-1, 1, rows).astype(np.float32)
+    chunks = (n + 1023) // 1024
+    d_col, d_x = torch.from_numpy(col).cuda(), torch.from_numpy(x).cuda()
+    out = torch.full((chunks,), float("nan"), dtype=torch.float32, device="cuda")
+    assert abi.sg_gather_sum(d_col.data_ptr(), d_x.data_ptr(), n, out.data_ptr()) == 0
+    got = out.cpu().numpy().astype(np.float64)
+    ref = np.array([x[col[c * 1024:(c + 1) * 1024]].astype(np.float64).sum() for c in range(chunks)])
+    mag = np.array([np.abs(x[col[c * 1024:(c + 1) * 1024]]).astype(np.float64).sum() for c in range(chunks)])
+    assert np.all(np.abs(got - ref) <= 1e-5 * mag + 1e-30)
+    assert abi.sg_gather_sum(d_col.data_ptr() + 4, d_x.data_ptr(), n, out.data_ptr()) == abi.SG_ERR_INVALID
 
 
 def _gemm(M, N, Kd, key, tile=None):
