@@ -363,6 +363,7 @@ __device__ bool gemm_chunk(const G& g, const uint16_t* __restrict__ A, const uin
 __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchDev B) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ uint64_t T[kGroups][64];
+  __shared__ uint32_t T32[kGroups][64];
   __shared__ uint64_t red[kGroups][kChunkThreads / 32 + 1];
   __shared__ uint64_t carry[kGroups];
   __shared__ Item cur[kGroups];
@@ -450,13 +451,17 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchDev B) {
       const uint64_t lk = stream_key(job.key, 1);
       uint8_t* lens = (uint8_t*)(base + L.y);   // row lengths, in y until the SpMV writes it
       if (it.phase == 0 && it.chunk < L.nchunks) {
-        if (g.t() < 64) T[gi][g.t()] = B.tables[64ull * job.p2 + g.t()];
+        if (g.t() < 64) {
+          const uint64_t t = B.tables[64ull * job.p2 + g.t()];
+          T[gi][g.t()] = t;
+          T32[gi][g.t()] = table_u32(t);
+        }
         g.sync();
       }
       if (digest) {
         digest_chunk(g, (const uint32_t*)(base + L.y), rows, B.keep + it.job, it.chunk);
       } else if (it.phase == 0) {
-        if (it.chunk < L.nchunks) spmv_chunk_sum(g, T[gi], lk, rows, lens, scan, it.chunk, red[gi]);
+        if (it.chunk < L.nchunks) spmv_chunk_sum(g, T[gi], T32[gi], lk, rows, lens, scan, it.chunk, red[gi]);
         else spmv_fill_chunk(g, (int32_t*)(base + L.col), (float*)(base + L.val), (float*)(base + L.x), cap, rows,
                              stream_key(job.key, 2), stream_key(job.key, 3), stream_key(job.key, 4),
                              it.chunk - L.nchunks);

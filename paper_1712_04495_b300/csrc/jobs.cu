@@ -69,11 +69,16 @@ __global__ void __launch_bounds__(kChunkThreads) k_spmv_chunk_sums(const uint64_
                                                                    uint8_t* __restrict__ lens,
                                                                    uint64_t* __restrict__ scan, uint64_t nchunks) {
   __shared__ uint64_t T[64];
+  __shared__ uint32_t T32[64];
   __shared__ uint64_t red[kChunkThreads / 32];
-  if (threadIdx.x < 64) T[threadIdx.x] = table[threadIdx.x];
+  if (threadIdx.x < 64) {
+    const uint64_t t = table[threadIdx.x];
+    T[threadIdx.x] = t;
+    T32[threadIdx.x] = table_u32(t);
+  }
   __syncthreads();
   for (uint64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x)
-    spmv_chunk_sum(BlockGroup{}, T, len_key, rows, lens, scan, ch, red);
+    spmv_chunk_sum(BlockGroup{}, T, T32, len_key, rows, lens, scan, ch, red);
 }
 
 __global__ void __launch_bounds__(kChunkThreads) k_spmv_scan_chunks(uint64_t* __restrict__ scan, uint64_t n) {

@@ -221,13 +221,24 @@ __device__ __forceinline__ void spmv_chunk(const G& g, const PtrT* __restrict__ 
 }
 
 // ------------------------------------------------------ SpMV CSR build
-// Row length: number of table thresholds <= the row's 32-bit uniform.
-__device__ __forceinline__ uint32_t row_len(const uint64_t* T, uint64_t len_key, uint64_t r) {
-  uint64_t u = sm64_at(len_key, r) >> 32;
+// Row length: number of table thresholds <= the row's 32-bit uniform u.
+// T32 is T saturated to 32 bits (2^32 - 1 for thresholds at or above 2^32):
+// for every u below 2^32 - 1 it gives the same count with 32-bit compares;
+// u = 2^32 - 1 takes the 64-bit table.
+__device__ __forceinline__ uint32_t table_u32(uint64_t t) { return (t >> 32) ? 0xFFFFFFFFu : (uint32_t)t; }
+
+__device__ __forceinline__ uint32_t row_len(const uint64_t* T, const uint32_t* T32, uint64_t len_key, uint64_t r) {
+  const uint32_t u = (uint32_t)(sm64_at(len_key, r) >> 32);
   uint32_t pos = 0;
+  if (u != 0xFFFFFFFFu) {
 #pragma unroll
-  for (uint32_t step = 32; step; step >>= 1)
-    if (T[pos + step - 1] <= u) pos += step;
+    for (uint32_t step = 32; step; step >>= 1)
+      if (T32[pos + step - 1] <= u) pos += step;
+  } else {
+#pragma unroll
+    for (uint32_t step = 32; step; step >>= 1)
+      if (T[pos + step - 1] <= (uint64_t)u) pos += step;
+  }
   return pos;
 }
 
@@ -250,9 +261,10 @@ __device__ __forceinline__ uint64_t block_sum_u64(const G& g, uint64_t v, uint64
 // array, free until the SpMV writes y; the row_ptr pass reads the lengths
 // back instead of hashing every row a second time. The last thread of a
 // ragged chunk writes zeros past the last row, inside y (4 bytes per row,
-// rounded up to 256). T in shared memory.
+// rounded up to 256). T and T32 (its 32-bit saturation) in shared memory.
 template <class G>
-__device__ __forceinline__ void spmv_chunk_sum(const G& g, const uint64_t* T, uint64_t len_key, uint64_t rows,
+__device__ __forceinline__ void spmv_chunk_sum(const G& g, const uint64_t* T, const uint32_t* T32, uint64_t len_key,
+                                               uint64_t rows,
                                                uint8_t* __restrict__ lens, uint64_t* __restrict__ scan,
                                                uint64_t chunk, uint64_t* red) {
   constexpr int kPer = kRowsPerScanChunk / kChunkThreads;
@@ -263,7 +275,7 @@ __device__ __forceinline__ void spmv_chunk_sum(const G& g, const uint64_t* T, ui
     uint32_t w[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
     for (int k = 0; k < kPer; k++) {
-      const uint32_t l = (r0 + k < rows) ? row_len(T, len_key, r0 + k) : 0u;
+      const uint32_t l = (r0 + k < rows) ? row_len(T, T32, len_key, r0 + k) : 0u;
       w[k >> 2] |= l << (8 * (k & 3));
       sum += l;
     }
