@@ -4,9 +4,12 @@
     python -m paper_1712_04495_b300.kernel_cases spmv  [rows, default 1e7]   [launches]
     python -m paper_1712_04495_b300.kernel_cases triad [n, default 64M]      [launches]
     python -m paper_1712_04495_b300.kernel_cases fill  [rows, default 1e7]   [launches]
+    python -m paper_1712_04495_b300.kernel_cases gather [rows, default 1e7]  [launches]
     python -m paper_1712_04495_b300.kernel_cases batch [jobs, default 10000] [launches]
     python -m paper_1712_04495_b300.kernel_cases replay [jobs, default 10000] [launches] [policy]
 
+`gather` times the gather-rate measurement kernel (sg_gather_sum) on the
+generated SpMV matrix's own columns and x, after one SpMV launch.
 `batch` runs the tiny-job trace (10,000 jobs, 2 GiB pool) through the
 persistent grouped kernel on the device engine's replay plan. `replay` runs
 the device engine's replay (one warp, logical clock) of the same trace.
@@ -51,7 +54,7 @@ def run(kind: str, size: int | None = None, launches: int = 3, tile: str | None 
                    launches)
         return {"kernel": "gemm", "tile": abi.gemm_tile_name(code), "size": m, "ms": ms,
                 "tflops": 2.0 * m ** 3 / (ms * 1e-3) / 1e12}
-    if kind in ("spmv", "fill"):
+    if kind in ("spmv", "fill", "gather"):
         rows = size or 10_000_000
         lam = 16.0
         cap = tg.spmv_nnz_cap(rows, lam)
@@ -68,6 +71,12 @@ def run(kind: str, size: int | None = None, launches: int = 3, tile: str | None 
         ptr_t = torch.int64 if lay["ptr64"] else torch.int32
         esz = 8 if lay["ptr64"] else 4
         nnz = int(base[lay["row_ptr"] + esz * rows:lay["row_ptr"] + esz * (rows + 1)].view(ptr_t).item())
+        if kind == "gather":
+            assert abi.sg_spmv(p + lay["row_ptr"], lay["ptr64"], p + lay["col"], p + lay["val"],
+                               p + lay["x"], p + lay["y"], rows, st) == 0
+            out = torch.empty((nnz + 1023) // 1024, dtype=torch.float32, device="cuda")
+            ms = _time(lambda: abi.sg_gather_sum(p + lay["col"], p + lay["x"], nnz, out.data_ptr(), st), launches)
+            return {"kernel": "gather", "rows": rows, "nnz": nnz, "ms": ms, "gathers_per_s": nnz / (ms * 1e-3)}
         ms = _time(lambda: abi.sg_spmv(p + lay["row_ptr"], lay["ptr64"], p + lay["col"], p + lay["val"],
                                        p + lay["x"], p + lay["y"], rows, st), launches)
         alg = esz * (rows + 1) + 8 * nnz + 8 * rows
