@@ -124,6 +124,31 @@ def test_poisson_table_matches_scipy_quantiles():
         assert np.array_equal(lens, ref.astype(np.int64))
 
 
+def test_row_length_search_in_32_bits_is_exact():
+    """The CUDA CSR build counts a row's length with 32-bit compares against
+    the table saturated to 2^32 - 1, and with the 64-bit table only for the
+    uniform 2^32 - 1. A model of that search gives the 64-bit count for every
+    uniform at and around each threshold of both Poisson tables used."""
+    for lam in (8.0, 16.0):
+        T = tg.poisson_cdf_table(lam).astype(np.uint64)
+        T32 = np.where(T >> np.uint64(32), np.uint64(0xFFFFFFFF), T)
+        cand = {0, 1, 0xFFFFFFFE, 0xFFFFFFFF}
+        for t in T.tolist():
+            cand.update(v for v in (t - 1, t, t + 1) if 0 <= v <= 0xFFFFFFFF)
+        for u in sorted(cand):
+            want = int(np.sum(T <= np.uint64(u)))
+            pos = 0
+            step = 32
+            while step:
+                if u != 0xFFFFFFFF:
+                    if T32[pos + step - 1] <= u:
+                        pos += step
+                elif T[pos + step - 1] <= u:
+                    pos += step
+                step >>= 1
+            assert pos == want, (lam, u, pos, want)
+
+
 def test_row_length_statistics():
     t = tg.poisson_cdf_table(16.0)
     lens = tg.row_lengths(99, np.arange(200000, dtype=np.uint64), t)
