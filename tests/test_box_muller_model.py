@@ -71,7 +71,8 @@ def test_sin_cos_of_2pi_u2_every_input():
     big_s, big_c = np.abs(rs) > 1e-6, np.abs(rc) > 1e-6
     assert _ulps(sin_v[big_s], rs[big_s]).max() <= 2.0
     assert _ulps(cos_v[big_c], rc[big_c]).max() <= 2.0
-    # near the zeros the values are exact multiples of pi/2 apart: absolute error far below 1e-12
+    # at the zeros of sine and cosine (angles at multiples of pi/2) the model gives exact
+    # zeros where fp64 leaves a remainder below 1e-12
     assert np.abs(sin_v.astype(np.float64) - rs).max() < 1e-6
     assert np.abs(sin_v[~big_s].astype(np.float64) - rs[~big_s]).max() < 1e-12
     assert np.abs(cos_v[~big_c].astype(np.float64) - rc[~big_c]).max() < 1e-12
