@@ -255,9 +255,12 @@ __device__ void publish_service(const BatchDev& B, GrantQueue* Q) {
   }
 }
 
-// Claim the next slot; 1 = item in *out, 0 = nothing left, -1 = gave up.
-__device__ int pop(const BatchDev& B, Item* out) {
-  const uint64_t pos = atomicAdd(&B.ctr[0], 1ull);
+// Claim the next slot of the queue (one thread).
+__device__ __forceinline__ uint64_t claim(const BatchDev& B) { return atomicAdd(&B.ctr[0], 1ull); }
+
+// The item in claimed slot pos, once published: 1 = item in *out, 0 =
+// nothing left, -1 = gave up.
+__device__ int fetch(const BatchDev& B, uint64_t pos, Item* out) {
   if (pos >= B.total) return 0;
   const uint32_t want = (uint32_t)(pos + 1);
   uint64_t t0 = 0;
@@ -405,8 +408,19 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchDev B) {
     else publish_service(B, &gq);
   }
 
+  // Thread 0 of a worker claims its next slot as soon as it has its current
+  // item, so the claim's round trip overlaps the item's work. A claimed slot
+  // is waited for only after the current item is done, as before: every
+  // worker holds at most one slot that is not yet published.
+  uint64_t next_slot = 0;
+  bool have_next = false;
   for (; !service;) {
-    if (g.t() == 0) action[gi] = pop(B, &cur[gi]);
+    if (g.t() == 0) {
+      const uint64_t pos = have_next ? next_slot : claim(B);
+      action[gi] = fetch(B, pos, &cur[gi]);
+      have_next = action[gi] == 1;
+      if (have_next) next_slot = claim(B);
+    }
     g.sync();
     if (action[gi] != 1) break;
     const Item it = cur[gi];
