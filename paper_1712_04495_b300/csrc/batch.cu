@@ -51,6 +51,14 @@ constexpr uint32_t kGemmSmem = 32 * 1024;           // per worker: A 16 KiB + B 
 constexpr uint32_t kBatchSmem = kGroups * kGemmSmem + 1024;
 constexpr uint32_t kBatchTmemCols = 512;
 constexpr uint32_t kGemmBM = 128;
+// Chunks one queue item carries, per phase: a tiny job's chunk is often
+// less work than the queue round trips that hand it out. SpMV: chunks of
+// kSpmvRowsChunk rows; triad and its generator: kTriadChunk elements; bf16
+// generator: kBf16Chunk elements; SpMV generator: kFillChunk non-zeros.
+constexpr uint64_t kSpmvChunksPerItem = 8;
+constexpr uint64_t kTriadChunksPerItem = 4;
+constexpr uint64_t kBf16ChunksPerItem = 8;
+constexpr uint64_t kFillChunksPerItem = 4;
 
 struct Item {
   uint32_t job, phase;
@@ -92,22 +100,22 @@ __host__ __device__ inline uint64_t cdiv(uint64_t a, uint64_t b) { return (a + b
 // chunks of phase `ph` of job `j` (the digest phase comes last when kept)
 __host__ __device__ inline uint64_t phase_chunks(const sg_job& j, uint32_t ph) {
   if (j.kind == SG_KIND_TRIAD) {
-    if (ph <= 1) return cdiv(j.p0, kTriadChunk);
+    if (ph <= 1) return cdiv(cdiv(j.p0, kTriadChunk), kTriadChunksPerItem);
     return cdiv(j.p0, kDigestChunk);
   }
   if (j.kind == SG_KIND_GEMM) {
     const uint64_t m = j.p0, n = j.p1, k = j.p2;
-    if (ph == 0) return cdiv(m * k, kBf16Chunk) + cdiv(n * k, kBf16Chunk);
+    if (ph == 0) return cdiv(cdiv(m * k, kBf16Chunk) + cdiv(n * k, kBf16Chunk), kBf16ChunksPerItem);
     if (ph == 1) return cdiv(m, kGemmBM) * cdiv(n, gemm_bn_small(n));
     return cdiv(m * n, kDigestChunk);
   }
   const uint64_t rows = j.p0, cap = j.p1;
   const uint64_t nch = cdiv(rows, kRowsPerScanChunk);
   switch (ph) {
-    case 0: return nch + cdiv(cap > 4 * rows ? cap : 4 * rows, kFillChunk);
+    case 0: return nch + cdiv(cdiv(cap > 4 * rows ? cap : 4 * rows, kFillChunk), kFillChunksPerItem);
     case 1: return 1;
     case 2: return nch;
-    case 3: return cdiv(rows, kSpmvRowsChunk);
+    case 3: return cdiv(rows, kSpmvRowsChunk * kSpmvChunksPerItem);
     default: return cdiv(rows, kDigestChunk);
   }
 }
@@ -436,9 +444,15 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchDev B) {
       float* b = a + n;
       float* c = b + n;
       const int vec = (n & 3) == 0;            // b and c 16-byte aligned (the grant is)
-      if (digest) digest_chunk(g, (const uint32_t*)a, n, B.keep + it.job, it.chunk);
-      else if (it.phase == 0) gen_triad_chunk(g, b, c, n, stream_key(job.key, 1), stream_key(job.key, 2), vec, it.chunk);
-      else triad_chunk(g, a, b, c, 3.0f, n, vec, it.chunk);
+      if (digest) {
+        digest_chunk(g, (const uint32_t*)a, n, B.keep + it.job, it.chunk);
+      } else {
+        const uint64_t c1 = cdiv(n, kTriadChunk);
+        for (uint64_t q = it.chunk * kTriadChunksPerItem; q < c1 && q < (it.chunk + 1) * kTriadChunksPerItem; q++) {
+          if (it.phase == 0) gen_triad_chunk(g, b, c, n, stream_key(job.key, 1), stream_key(job.key, 2), vec, q);
+          else triad_chunk(g, a, b, c, 3.0f, n, vec, q);
+        }
+      }
     } else if (job.kind == SG_KIND_GEMM) {
       const uint32_t m = (uint32_t)job.p0, n = (uint32_t)job.p1, k = job.p2;
       const GemmLayoutHD L = gemm_layout_hd(m, n, k);
@@ -448,9 +462,11 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchDev B) {
       if (digest) {
         digest_chunk(g, (const uint32_t*)C, (uint64_t)m * n, B.keep + it.job, it.chunk);
       } else if (it.phase == 0) {
-        const uint64_t ca = cdiv((uint64_t)m * k, kBf16Chunk);
-        if (it.chunk < ca) gen_bf16_chunk(g, A, (uint64_t)m * k, stream_key(job.key, 1), it.chunk);
-        else gen_bf16_chunk(g, Bt, (uint64_t)n * k, stream_key(job.key, 2), it.chunk - ca);
+        const uint64_t ca = cdiv((uint64_t)m * k, kBf16Chunk), c1 = ca + cdiv((uint64_t)n * k, kBf16Chunk);
+        for (uint64_t q = it.chunk * kBf16ChunksPerItem; q < c1 && q < (it.chunk + 1) * kBf16ChunksPerItem; q++) {
+          if (q < ca) gen_bf16_chunk(g, A, (uint64_t)m * k, stream_key(job.key, 1), q);
+          else gen_bf16_chunk(g, Bt, (uint64_t)n * k, stream_key(job.key, 2), q - ca);
+        }
       } else if (gemm_bn_small(n) == 128) {
         ok = gemm_chunk<128>(g, A, Bt, C, m, n, k, it.chunk, sa, tmem, smem_u32(&mbar[gi]), mphase, &s_abort,
                              &vote[gi]);
@@ -476,9 +492,13 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchDev B) {
         digest_chunk(g, (const uint32_t*)(base + L.y), rows, B.keep + it.job, it.chunk);
       } else if (it.phase == 0) {
         if (it.chunk < L.nchunks) spmv_chunk_sum(g, T[gi], T32[gi], lk, rows, lens, scan, it.chunk, red[gi]);
-        else spmv_fill_chunk(g, (int32_t*)(base + L.col), (float*)(base + L.val), (float*)(base + L.x), cap, rows,
-                             stream_key(job.key, 2), stream_key(job.key, 3), stream_key(job.key, 4),
-                             it.chunk - L.nchunks);
+        else {
+          const uint64_t f1 = cdiv(cap > 4 * rows ? cap : 4 * rows, kFillChunk);
+          const uint64_t f0 = (it.chunk - L.nchunks) * kFillChunksPerItem;
+          for (uint64_t q = f0; q < f1 && q < f0 + kFillChunksPerItem; q++)
+            spmv_fill_chunk(g, (int32_t*)(base + L.col), (float*)(base + L.val), (float*)(base + L.x), cap, rows,
+                            stream_key(job.key, 2), stream_key(job.key, 3), stream_key(job.key, 4), q);
+        }
       } else if (it.phase == 1) {
         spmv_scan(g, scan, L.nchunks, red[gi], &carry[gi]);
       } else if (it.phase == 2) {
@@ -489,14 +509,17 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchDev B) {
           spmv_row_ptr_chunk<SubGroup, int32_t>(g, lens, rows, scan, L.nchunks, (int32_t*)(base + L.row_ptr),
                                                 cap, B.err, it.chunk, red[gi]);
       } else {
-        if (L.ptr64)
-          spmv_chunk<SubGroup, int64_t>(g, (const int64_t*)(base + L.row_ptr), (const int32_t*)(base + L.col),
-                                        (const float*)(base + L.val), (const float*)(base + L.x),
-                                        (float*)(base + L.y), rows, 1, it.chunk);
-        else
-          spmv_chunk<SubGroup, int32_t>(g, (const int32_t*)(base + L.row_ptr), (const int32_t*)(base + L.col),
-                                        (const float*)(base + L.val), (const float*)(base + L.x),
-                                        (float*)(base + L.y), rows, 1, it.chunk);
+        const uint64_t c1 = cdiv(rows, kSpmvRowsChunk);
+        for (uint64_t c = it.chunk * kSpmvChunksPerItem; c < c1 && c < (it.chunk + 1) * kSpmvChunksPerItem; c++) {
+          if (L.ptr64)
+            spmv_chunk<SubGroup, int64_t>(g, (const int64_t*)(base + L.row_ptr), (const int32_t*)(base + L.col),
+                                          (const float*)(base + L.val), (const float*)(base + L.x),
+                                          (float*)(base + L.y), rows, 1, c);
+          else
+            spmv_chunk<SubGroup, int32_t>(g, (const int32_t*)(base + L.row_ptr), (const int32_t*)(base + L.col),
+                                          (const float*)(base + L.val), (const float*)(base + L.x),
+                                          (float*)(base + L.y), rows, 1, c);
+        }
       }
     }
     if (!ok) {
