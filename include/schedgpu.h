@@ -555,10 +555,11 @@ int sg_spmv(const void* row_ptr, int ptr64, const int32_t* col, const float* val
  * `base` (row_ptr, col, val, x, y, scan workspace; each 256-byte aligned;
  * col / val sized for nnz_cap entries, row_ptr int64 when nnz_cap >= 2^31):
  * row lengths by inverse CDF on table_dev (64 uint64 thresholds), columns
- * uniform in [0, rows), values N(0,1), x uniform[-1,1). If the generated
- * row lengths sum to more than nnz_cap, row_ptr is clamped to nnz_cap and
- * a flag is OR-ed into err_dev (uint32, may be NULL). The scan workspace is
- * scratch inside the layout. */
+ * uniform in [0, rows), values N(0,1), x uniform[-1,1). Columns and values
+ * are written for all nnz_cap slots (those past the matrix's non-zeros are
+ * never read). If the generated row lengths sum to more than nnz_cap,
+ * row_ptr is clamped to nnz_cap and a flag is OR-ed into err_dev (uint32,
+ * may be NULL). The scan workspace and y are scratch until the SpMV. */
 int sg_gen_spmv(void* base, uint64_t rows, uint64_t nnz_cap, const uint64_t* table_dev,
                 uint64_t key, uint32_t* err_dev, void* stream);
 

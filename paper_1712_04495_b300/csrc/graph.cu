@@ -3,9 +3,9 @@
 // The device replay (sg_replay) decides, on the logical clock with declared
 // durations, where each job lives in the pool and in what order jobs are
 // granted. This file turns that plan into one CUDA graph: every job is a
-// child graph (its generator kernels, then its kernel, then optionally its
-// output digest), and a job depends on every job that used any byte of its
-// extent before it in grant order. Jobs that share no memory run
+// chain of kernel nodes (its generator kernels, then its kernel, then
+// optionally its output digest), and a job depends on every job that used
+// any byte of its extent before it in grant order. Jobs that share no memory run
 // concurrently; jobs that share memory never overlap in time, so the graph
 // is memory-safe by construction and needs no engine at run time. The
 // graph is built and instantiated once and replayed as one launch.
@@ -37,37 +37,49 @@ extern "C" int sg_graph_build(void* dev_pool, uint64_t pool_bytes, const sg_job*
   if (rc != SG_OK) return rc;
   sg_graph* g = new sg_graph();
   cudaStream_t cap = nullptr;
-  std::vector<cudaGraphNode_t> node(n, nullptr);
+  std::vector<cudaGraphNode_t> tail(n, nullptr);   // each job's last node
   std::vector<cudaGraphNode_t> deps;
   RelHook none;
   memset(&none, 0, sizeof none);
   rc = SG_OK;
   do {
-    if (cudaGraphCreate(&g->graph, 0) != cudaSuccess) { rc = SG_ERR_CUDA; break; }
     if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) { rc = SG_ERR_CUDA; break; }
+    // One capture for the whole batch: before each job the stream's capture
+    // dependencies are set to the last nodes of the jobs it depends on, so
+    // the job's kernels hang from exactly those (a root when there are
+    // none), and its own kernels follow one another.
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { rc = SG_ERR_CUDA; break; }
     for (uint32_t j : pd.order) {
       const uint64_t off = plan[j].offset;
       deps.clear();
-      for (uint64_t e = pd.pred_ptr[j]; e < pd.pred_ptr[j + 1]; e++) deps.push_back(node[pd.pred[e]]);
-      cudaGraph_t child = nullptr;
-      if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { rc = SG_ERR_CUDA; break; }
+      for (uint64_t e = pd.pred_ptr[j]; e < pd.pred_ptr[j + 1]; e++) deps.push_back(tail[pd.pred[e]]);
+      if (cudaStreamUpdateCaptureDependencies(cap, deps.data(), nullptr, deps.size(),
+                                              cudaStreamSetCaptureDependencies) != cudaSuccess) {
+        rc = SG_ERR_CUDA;
+        break;
+      }
       uint64_t nl = 0;
       int lrc = launch_job(jobs[j], (char*)dev_pool + off, tables_dev, none, keep_dev ? keep_dev + j : nullptr,
                            nullptr, cap, &nl);
-      cudaError_t ec = cudaStreamEndCapture(cap, &child);
-      if (lrc != SG_OK || ec != cudaSuccess) {
-        if (child) cudaGraphDestroy(child);
-        rc = lrc != SG_OK ? lrc : SG_ERR_CUDA;
+      if (lrc != SG_OK) { rc = lrc; break; }
+      cudaStreamCaptureStatus cs;
+      const cudaGraphNode_t* d = nullptr;
+      size_t nd = 0;
+      if (cudaStreamGetCaptureInfo(cap, &cs, nullptr, nullptr, &d, nullptr, &nd) != cudaSuccess ||
+          cs != cudaStreamCaptureStatusActive || nd != 1) {
+        rc = SG_ERR_CUDA;
         break;
       }
-      cudaError_t ea = cudaGraphAddChildGraphNode(&node[j], g->graph, deps.data(), deps.size(), child);
-      cudaGraphDestroy(child);
-      if (ea != cudaSuccess) { rc = SG_ERR_CUDA; break; }
+      tail[j] = d[0];
       g->kernels += nl;
       g->edges += deps.size();
       g->jobs++;
     }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(cap, &graph);   // ends the capture on every path
+    g->graph = graph;
     if (rc != SG_OK) break;
+    if (ec != cudaSuccess || !graph) { rc = SG_ERR_CUDA; break; }
     if (cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) { rc = SG_ERR_CUDA; break; }
   } while (0);
   if (cap) cudaStreamDestroy(cap);

@@ -64,23 +64,6 @@ __global__ void __launch_bounds__(kChunkThreads, 6) k_spmv(const PtrT* __restric
   job_epilogue(hook);
 }
 
-__global__ void __launch_bounds__(kChunkThreads) k_spmv_chunk_sums(const uint64_t* __restrict__ table,
-                                                                   uint64_t len_key, uint64_t rows,
-                                                                   uint8_t* __restrict__ lens,
-                                                                   uint64_t* __restrict__ scan, uint64_t nchunks) {
-  __shared__ uint64_t T[64];
-  __shared__ uint32_t T32[64];
-  __shared__ uint64_t red[kChunkThreads / 32];
-  if (threadIdx.x < 64) {
-    const uint64_t t = table[threadIdx.x];
-    T[threadIdx.x] = t;
-    T32[threadIdx.x] = table_u32(t);
-  }
-  __syncthreads();
-  for (uint64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x)
-    spmv_chunk_sum(BlockGroup{}, T, T32, len_key, rows, lens, scan, ch, red);
-}
-
 __global__ void __launch_bounds__(kChunkThreads) k_spmv_scan_chunks(uint64_t* __restrict__ scan, uint64_t n) {
   __shared__ uint64_t wsum[kChunkThreads / 32 + 1];
   __shared__ uint64_t carry;
@@ -97,20 +80,48 @@ __global__ void __launch_bounds__(kChunkThreads) k_spmv_row_ptr(const uint8_t* _
     spmv_row_ptr_chunk<BlockGroup, PtrT>(BlockGroup{}, lens, rows, scan, nchunks, row_ptr, cap, err, ch, wsum);
 }
 
-__global__ void __launch_bounds__(kChunkThreads) k_spmv_fill(int32_t* __restrict__ col, float* __restrict__ val,
-                                                             float* __restrict__ x, const uint64_t* total,
+// The SpMV generator's first launch: the row lengths of the scan chunks
+// (blocks [0, nchunks)) and, independent of them, the columns and values of
+// all cap non-zero slots and x (the other blocks). Slots past the matrix's
+// non-zeros get values too and are never read.
+__global__ void __launch_bounds__(kChunkThreads) k_spmv_fill(const uint64_t* __restrict__ table, uint64_t len_key,
+                                                             uint8_t* __restrict__ lens, uint64_t* __restrict__ scan,
+                                                             uint64_t nchunks, int32_t* __restrict__ col,
+                                                             float* __restrict__ val, float* __restrict__ x,
                                                              uint64_t cap, uint64_t rows, uint64_t kc,
                                                              uint64_t kv, uint64_t kx) {
-  const uint64_t nnz = *total < cap ? *total : cap;
-  const uint64_t nch = spmv_fill_chunks(cap, rows);
-  for (uint64_t ch = blockIdx.x; ch < nch; ch += gridDim.x)
-    spmv_fill_chunk(BlockGroup{}, col, val, x, nnz, rows, kc, kv, kx, ch);
+  __shared__ uint64_t T[64];
+  __shared__ uint32_t T32[64];
+  __shared__ uint64_t red[kChunkThreads / 32];
+  if (threadIdx.x < 64) {
+    const uint64_t t = table[threadIdx.x];
+    T[threadIdx.x] = t;
+    T32[threadIdx.x] = table_u32(t);
+  }
+  __syncthreads();
+  const uint64_t nch = nchunks + spmv_fill_chunks(cap, rows);
+  for (uint64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+    if (ch < nchunks) spmv_chunk_sum(BlockGroup{}, T, T32, len_key, rows, lens, scan, ch, red);
+    else spmv_fill_chunk(BlockGroup{}, col, val, x, cap, rows, kc, kv, kx, ch - nchunks);
+  }
 }
 
 __global__ void __launch_bounds__(kChunkThreads) k_gen_bf16(uint16_t* __restrict__ out, uint64_t count,
                                                             uint64_t key) {
   const uint64_t nch = (count + kBf16Chunk - 1) / kBf16Chunk;
   for (uint64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) gen_bf16_chunk(BlockGroup{}, out, count, key, ch);
+}
+
+// Both GEMM operands in one launch: the chunks of A, then those of Bt.
+__global__ void __launch_bounds__(kChunkThreads) k_gen_gemm(uint16_t* __restrict__ A, uint64_t count_a, uint64_t key_a,
+                                                            uint16_t* __restrict__ Bt, uint64_t count_b,
+                                                            uint64_t key_b) {
+  const uint64_t na = (count_a + kBf16Chunk - 1) / kBf16Chunk;
+  const uint64_t nch = na + (count_b + kBf16Chunk - 1) / kBf16Chunk;
+  for (uint64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+    if (ch < na) gen_bf16_chunk(BlockGroup{}, A, count_a, key_a, ch);
+    else gen_bf16_chunk(BlockGroup{}, Bt, count_b, key_b, ch - na);
+  }
 }
 
 // Measurement kernel, not a step of a job: the random-gather rate that
@@ -198,7 +209,10 @@ int launch_gen_spmv(char* base, uint64_t rows, uint64_t nnz, const uint64_t* tab
   uint64_t lk = stream_key(key, 1);
   unsigned nch = (unsigned)L.nchunks;
   uint8_t* lens = (uint8_t*)(base + L.y);   // row lengths, in y until the SpMV writes it
-  k_spmv_chunk_sums<<<nch, kChunkThreads, 0, st>>>(table, lk, rows, lens, scan, L.nchunks);
+  k_spmv_fill<<<grid_for(L.nchunks * kFillChunk + spmv_fill_chunks(nnz, rows) * kFillChunk, kFillChunk),
+                kChunkThreads, 0, st>>>(table, lk, lens, scan, L.nchunks, (int32_t*)(base + L.col),
+                                        (float*)(base + L.val), (float*)(base + L.x), nnz, rows,
+                                        stream_key(key, 2), stream_key(key, 3), stream_key(key, 4));
   k_spmv_scan_chunks<<<1, kChunkThreads, 0, st>>>(scan, L.nchunks);
   if (L.ptr64)
     k_spmv_row_ptr<int64_t><<<nch, kChunkThreads, 0, st>>>(lens, rows, scan, L.nchunks,
@@ -206,10 +220,15 @@ int launch_gen_spmv(char* base, uint64_t rows, uint64_t nnz, const uint64_t* tab
   else
     k_spmv_row_ptr<int32_t><<<nch, kChunkThreads, 0, st>>>(lens, rows, scan, L.nchunks,
                                                            (int32_t*)(base + L.row_ptr), nnz, err);
-  k_spmv_fill<<<grid_for((nnz > 4 * rows ? nnz : 4 * rows), kFillChunk), kChunkThreads, 0, st>>>(
-      (int32_t*)(base + L.col), (float*)(base + L.val), (float*)(base + L.x), scan + L.nchunks, nnz,
-      rows, stream_key(key, 2), stream_key(key, 3), stream_key(key, 4));
-  if (launches) *launches += 4;
+  if (launches) *launches += 3;
+  return cudaPeekAtLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
+}
+
+int launch_gen_gemm(uint16_t* A, uint64_t count_a, uint64_t key_a, uint16_t* Bt, uint64_t count_b, uint64_t key_b,
+                    cudaStream_t st) {
+  if (!aligned16(A) || !aligned16(Bt)) return SG_ERR_INVALID;
+  k_gen_gemm<<<grid_for(count_a + count_b + kBf16Chunk, kBf16Chunk), kChunkThreads, 0, st>>>(A, count_a, key_a, Bt,
+                                                                                            count_b, key_b);
   return cudaPeekAtLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
 }
 
@@ -279,12 +298,12 @@ int launch_job(const sg_job& job, char* base, const uint64_t* tables, const RelH
       uint64_t m = job.p0, n = job.p1, k = job.p2;
       GemmLayout L = gemm_layout(m, n, k);
       if (L.total > job.need) return SG_ERR_INVALID;
-      rc = launch_gen_bf16((uint16_t*)(base + L.A), m * k, stream_key(job.key, 1), st);
-      if (rc == SG_OK) rc = launch_gen_bf16((uint16_t*)(base + L.B), n * k, stream_key(job.key, 2), st);
+      rc = launch_gen_gemm((uint16_t*)(base + L.A), m * k, stream_key(job.key, 1), (uint16_t*)(base + L.B), n * k,
+                           stream_key(job.key, 2), st);
       if (rc == SG_OK)
         rc = launch_gemm((const uint16_t*)(base + L.A), (const uint16_t*)(base + L.B),
                          (float*)(base + L.C), (uint32_t)m, (uint32_t)n, (uint32_t)k, last, st);
-      nl = 3;
+      nl = 2;
       out = base + L.C;
       out_words = m * n;
       break;
@@ -339,9 +358,8 @@ extern "C" int sg_gen_spmv(void* base, uint64_t rows, uint64_t nnz, const uint64
 extern "C" int sg_gen_gemm(uint16_t* A, uint16_t* Bt, uint32_t M, uint32_t N, uint32_t K, uint64_t key,
                            void* stream) {
   if (!A || !Bt) return SG_ERR_INVALID;
-  int rc = launch_gen_bf16(A, (uint64_t)M * K, stream_key(key, 1), (cudaStream_t)stream);
-  if (rc == SG_OK) rc = launch_gen_bf16(Bt, (uint64_t)N * K, stream_key(key, 2), (cudaStream_t)stream);
-  return rc;
+  return launch_gen_gemm(A, (uint64_t)M * K, stream_key(key, 1), Bt, (uint64_t)N * K, stream_key(key, 2),
+                         (cudaStream_t)stream);
 }
 
 extern "C" int sg_gather_sum(const int32_t* col, const float* x, uint64_t n, float* out_dev, void* stream) {

@@ -421,7 +421,7 @@ __device__ __forceinline__ void spmv_fill_chunk(const G& g, int32_t* __restrict_
   }
 }
 
-__device__ __forceinline__ uint64_t spmv_fill_chunks(uint64_t nnz_cap, uint64_t rows) {
+__host__ __device__ __forceinline__ uint64_t spmv_fill_chunks(uint64_t nnz_cap, uint64_t rows) {
   const uint64_t need = nnz_cap > 4 * rows ? nnz_cap : 4 * rows;
   return (need + kFillChunk - 1) / kFillChunk;
 }
