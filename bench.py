@@ -1111,7 +1111,7 @@ def main():
             extra["serving"] = serving_section(torch, abi, runtime, args.serving_requests)
             extra["configs"] = configs_section(torch, abi, runtime)
         # the kernel with the largest share of a step's ncu launch list is the
-        # CSR SpMV (30.2% of a step's kernel time), just ahead of the GEMM (29.2%)
+        # CSR SpMV (30.8% of a step's kernel time), just ahead of the GEMM (28.9%)
         extra["roofline"] = {k: kr["spmv"][k] for k in ("bound", "achieved", "peak", "unit", "frac",
                                                         "traffic")}
         extra["roofline"]["kernel"] = kr["spmv"]["kernel"]
