@@ -342,48 +342,67 @@ __device__ __forceinline__ void rec_store(const Eng& E, uint32_t j, const sg_rec
   for (int i = 0; i < 6; i++) est(E, p + i, w[i]);
 }
 
-// Write a ticket's record to the device log and, in real runs, to the
-// host-mapped copy (status last, after a system fence).
+// Host-mapped publication (real runs). The host reads a record's fields
+// once it sees a flag: the record's status, the grant ring's tail or the
+// count of finished tickets. So each publication writes the fields first,
+// then one system fence, then its flags.
+
+// The host copy of a record's fields other than its status (lane 0, no fence).
+__device__ __forceinline__ void publish_fields(const Eng& E, uint32_t j, const sg_record& r) {
+  volatile sg_record* pr = E.pub_rec + j;
+  pr->slot = r.slot;
+  pr->grant_seq = r.grant_seq;
+  pr->grant_t = r.grant_t;
+  pr->offset = r.offset;
+  pr->done_t = r.done_t;
+  pr->arrival_t = r.arrival_t;
+}
+
+// A ticket's record: the device log and the host copy, status last.
 __device__ __forceinline__ void publish_record(const Eng& E, uint32_t j, const sg_record& r) {
   __syncwarp();
   if (lane_id() == 0) {
     rec_store(E, j, r);
     if (E.pub_rec) {
-      volatile sg_record* pr = E.pub_rec + j;
-      pr->slot = r.slot;
-      pr->grant_seq = r.grant_seq;
-      pr->grant_t = r.grant_t;
-      pr->offset = r.offset;
-      pr->done_t = r.done_t;
-      pr->arrival_t = r.arrival_t;
+      publish_fields(E, j, r);
       __threadfence_system();
-      pr->status = r.status;
+      ((volatile sg_record*)(E.pub_rec + j))->status = r.status;
     }
   }
   __syncwarp();
 }
 
-// Append a granted ticket to the host-mapped grant ring (real runs).
-__device__ __forceinline__ void publish_grant_ring(const Eng& E, Sess& s, uint32_t j) {
-  if (E.dev_ring) {
-    if (lane_id() == 0) est(E, E.dev_ring + s.ring_tail % s.cap, j);
-    __syncwarp();
-  }
-  if (E.pub_ring) {
-    if (lane_id() == 0) {
-      ((volatile uint32_t*)E.pub_ring)[s.ring_tail % s.cap] = j;
+// A grant: the record and the grant-ring entry, then one system fence, then
+// the two flags a host reads them by (the record's status, the ring tail).
+__device__ __forceinline__ void publish_grant(const Eng& E, Sess& s, uint32_t j, const sg_record& r) {
+  __syncwarp();
+  if (lane_id() == 0) {
+    rec_store(E, j, r);
+    if (E.dev_ring) est(E, E.dev_ring + s.ring_tail % s.cap, j);
+    if (E.pub_rec || E.pub_ring) {
+      if (E.pub_rec) publish_fields(E, j, r);
+      if (E.pub_ring) ((volatile uint32_t*)E.pub_ring)[s.ring_tail % s.cap] = j;
       __threadfence_system();
-      ((volatile uint32_t*)E.pub_hdr)[0] = s.ring_tail + 1;
+      if (E.pub_rec) ((volatile sg_record*)(E.pub_rec + j))->status = r.status;
+      if (E.pub_ring) ((volatile uint32_t*)E.pub_hdr)[0] = s.ring_tail + 1;
     }
-    __syncwarp();
   }
+  __syncwarp();
   s.ring_tail += 1;
 }
 
-__device__ __forceinline__ void publish_done_count(const Eng& E, const Sess& s) {
-  if (E.pub_hdr && lane_id() == 0) {
-    __threadfence_system();
-    ((volatile uint32_t*)E.pub_hdr)[2] = s.n_done;
+// A finished ticket: the record, one system fence, then its status and the
+// count of finished tickets.
+__device__ __forceinline__ void publish_finished(const Eng& E, const Sess& s, uint32_t j, const sg_record& r) {
+  __syncwarp();
+  if (lane_id() == 0) {
+    rec_store(E, j, r);
+    if (E.pub_rec || E.pub_hdr) {
+      if (E.pub_rec) publish_fields(E, j, r);
+      __threadfence_system();
+      if (E.pub_rec) ((volatile sg_record*)(E.pub_rec + j))->status = r.status;
+      if (E.pub_hdr) ((volatile uint32_t*)E.pub_hdr)[2] = s.n_done;
+    }
   }
   __syncwarp();
 }
@@ -477,8 +496,7 @@ __device__ __forceinline__ bool try_grant(const Eng& E, Sess& s, uint32_t j, uin
     est(E, E.status + j, (uint32_t)ST_RUNNING);
     est(E, E.blk_done + j, 0u);
   }
-  publish_record(E, j, r);
-  publish_grant_ring(E, s, j);
+  publish_grant(E, s, j, r);
   if (heap) heap_push(*heap, t + dur[j], ((uint64_t)EV_COMPLETE << 32) | j, s);
   return true;
 }
@@ -737,9 +755,8 @@ __device__ __forceinline__ void op_declare(const Eng& E, Sess& s, uint32_t j, ui
     // larger than the whole pool: refused at once, never queued
     r.status = ST_TOO_LARGE;
     if (lane_id() == 0) est(E, E.status + j, (uint32_t)ST_TOO_LARGE);
-    publish_record(E, j, r);
     s.n_done += 1;
-    publish_done_count(E, s);
+    publish_finished(E, s, j, r);
     return;
   }
   if (lane_id() == 0) rec_store(E, j, r);
@@ -749,13 +766,17 @@ __device__ __forceinline__ void op_declare(const Eng& E, Sess& s, uint32_t j, ui
   }
   q_insert(E, s, j);
   r.status = ST_QUEUED;
-  publish_record(E, j, r);
+  if (lane_id() == 0) rec_store(E, j, r);
+  __syncwarp();
   if (heap && timeout && timeout[j] != ~0ull) {
     uint64_t tt = t + timeout[j];
     if (tt < t) tt = ~0ull;
     heap_push(*heap, tt, ((uint64_t)EV_TIMEOUT << 32) | j, s);
   }
   policy_pass(E, s, t, heap, dur);
+  // the host's copy says QUEUED only if the pass left j waiting (a grant in
+  // the pass published it as RUNNING)
+  if (E.pub_rec && eld(E, E.status + j) == ST_QUEUED) publish_record(E, j, r);
 }
 
 // Post-free of `bytes` declared bytes of ticket j (0 or >= held: all).
@@ -789,8 +810,8 @@ __device__ __forceinline__ bool op_release(const Eng& E, Sess& s, uint32_t j, ui
     ext_give(E, s, freed_off, freed);
     s.used -= freed;
   }
-  publish_record(E, j, r);
-  publish_done_count(E, s);
+  if (all) publish_finished(E, s, j, r);
+  else publish_record(E, j, r);
   policy_pass(E, s, t, heap, dur);
   return true;
 }
@@ -807,8 +828,7 @@ __device__ __forceinline__ uint32_t op_cancel(const Eng& E, Sess& s, uint32_t j,
   r.done_t = t;
   if (lane_id() == 0) est(E, E.status + j, (uint32_t)ST_TIMEOUT);
   s.n_done += 1;
-  publish_record(E, j, r);
-  publish_done_count(E, s);
+  publish_finished(E, s, j, r);
   // removing the head can unblock FIFO: notify
   policy_pass(E, s, t, heap, dur);
   return ST_TIMEOUT;
