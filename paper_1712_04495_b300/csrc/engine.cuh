@@ -168,8 +168,11 @@ __device__ __forceinline__ bool eng_lock(const Eng& E, uint64_t limit_ns = 20000
     for (;;) {
       if (atomicCAS(&E.hdr->lock, 0u, 1u) == 0u) { ok = 1; break; }
       if (globaltimer_ns() - t0 > limit_ns) break;
+      // short naps: a holder keeps the lock for microseconds, and a waiter
+      // that sleeps longer than that lets the declaring kernel, which takes
+      // the lock again at once, win it over a job's release again and again
       __nanosleep(ns);
-      if (ns < 1024) ns <<= 1;
+      if (ns < 128) ns <<= 1;
     }
     if (!ok) {
       atomicOr(&E.hdr->err, ERR_LOCK);
