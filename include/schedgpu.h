@@ -547,9 +547,20 @@ int sg_gen_triad(float* b, float* c, uint64_t n, uint64_t key, void* stream);
 
 /* FP32 CSR SpMV y = A x. row_ptr: rows+1 entries, int32 (ptr64 = 0) or
  * int64 (ptr64 = 1); col int32, val fp32 (nnz each); x, y fp32 (rows).
- * Square matrix; device pointers. */
+ * Square matrix; device pointers. When x lies inside the pool of a live
+ * context (as it does for SpMV jobs, whose arrays sit in their grant), x is
+ * gathered through a texture window over that pool, otherwise with global
+ * loads; y is the same either way. */
 int sg_spmv(const void* row_ptr, int ptr64, const int32_t* col, const float* val,
             const float* x, float* y, uint64_t rows, void* stream);
+
+/* How sg_spmv (and every SpMV job) gathers an x of `rows` floats at device
+ * address x: SG_GATHER_TEXTURE through a texture window of a live context's
+ * pool, SG_GATHER_LOAD with global loads (x outside every pool, in a pool
+ * whose base is not texture-aligned, or too long for one window). */
+#define SG_GATHER_LOAD    0
+#define SG_GATHER_TEXTURE 1
+int sg_spmv_gather_path(const float* x, uint64_t rows);
 
 /* Build the CSR matrix and x of an SpMV job in its declared layout at
  * `base` (row_ptr, col, val, x, y, scan workspace; each 256-byte aligned;
@@ -611,10 +622,13 @@ int sg_gen_gemm(uint16_t* A, uint16_t* Bt, uint32_t M, uint32_t N, uint32_t K, u
  * counterpart): it times the random gathers x[col[i]] that bound the CSR
  * SpMV job kernel, on the SpMV's own columns. out_dev[c] = sum of
  * x[col[i]] over i in [1024 c, 1024 (c + 1)) for the ceil(n / 1024) chunks
- * c; col (int32, n entries, 16-byte aligned, every entry a valid index of
- * x), x (fp32) and out_dev are device arrays owned by the caller.
- * SG_ERR_INVALID for a null or misaligned col, a null x or out_dev. */
-int sg_gather_sum(const int32_t* col, const float* x, uint64_t n, float* out_dev, void* stream);
+ * c; col (int32, n entries, 16-byte aligned, every entry in [0, x_len)),
+ * x (fp32, x_len entries) and out_dev are device arrays owned by the
+ * caller. x is gathered the way sg_spmv gathers it (a texture window when x
+ * lies in a live context's pool, else loads). SG_ERR_INVALID for a null or
+ * misaligned col, a null x or out_dev. */
+int sg_gather_sum(const int32_t* col, const float* x, uint64_t x_len, uint64_t n, float* out_dev,
+                  void* stream);
 
 /* Order-independent 64-bit digest of `words` 32-bit words at dev_ptr:
  * sum over i of mix64((i << 32) | word_i), modulo 2^64, added into

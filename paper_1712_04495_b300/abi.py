@@ -143,7 +143,8 @@ _SIGS = {
     "sg_autotune_clear": ([], ctypes.c_int),
     "sg_gen_gemm": ([_P, _P, _U32, _U32, _U32, _U64, _P], ctypes.c_int),
     "sg_digest": ([_P, _U64, _P, _P], ctypes.c_int),
-    "sg_gather_sum": ([_P, _P, _U64, _P, _P], ctypes.c_int),
+    "sg_gather_sum": ([_P, _P, _U64, _U64, _P, _P], ctypes.c_int),
+    "sg_spmv_gather_path": ([_P, _U64], ctypes.c_int),
     "sg_cancel": ([_P, _U32, _P], ctypes.c_int),
     "sg_poll_grants": ([_P, _P, _P, _U32, _P], ctypes.c_int),
     "sg_server_start": ([_P, ctypes.c_char_p, _P], ctypes.c_int),
@@ -513,8 +514,17 @@ def sg_digest(ptr, words: int, out_ptr, stream: int = 0) -> int:
     return lib().sg_digest(ptr, words, out_ptr, stream)
 
 
-def sg_gather_sum(col, x, n: int, out_ptr, stream: int = 0) -> int:
-    return lib().sg_gather_sum(col, x, n, out_ptr, stream)
+SG_GATHER_LOAD, SG_GATHER_TEXTURE = 0, 1
+
+
+def sg_spmv_gather_path(x, rows: int) -> int:
+    """SG_GATHER_TEXTURE when x (rows floats) lies in a texture window of a
+    live context's pool, else SG_GATHER_LOAD."""
+    return lib().sg_spmv_gather_path(x, rows)
+
+
+def sg_gather_sum(col, x, x_len: int, n: int, out_ptr, stream: int = 0) -> int:
+    return lib().sg_gather_sum(col, x, x_len, n, out_ptr, stream)
 
 
 # ------------------------------------------------ shared memory (no server)

@@ -512,12 +512,12 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchDev B) {
         const uint64_t c1 = cdiv(rows, kSpmvRowsChunk);
         for (uint64_t c = it.chunk * kSpmvChunksPerItem; c < c1 && c < (it.chunk + 1) * kSpmvChunksPerItem; c++) {
           if (L.ptr64)
-            spmv_chunk<SubGroup, int64_t>(g, (const int64_t*)(base + L.row_ptr), (const int32_t*)(base + L.col),
-                                          (const float*)(base + L.val), (const float*)(base + L.x),
+            spmv_chunk<SubGroup, int64_t, XLoadL2>(g, (const int64_t*)(base + L.row_ptr), (const int32_t*)(base + L.col),
+                                          (const float*)(base + L.val), XLoadL2{(const float*)(base + L.x)},
                                           (float*)(base + L.y), rows, 1, c);
           else
-            spmv_chunk<SubGroup, int32_t>(g, (const int32_t*)(base + L.row_ptr), (const int32_t*)(base + L.col),
-                                          (const float*)(base + L.val), (const float*)(base + L.x),
+            spmv_chunk<SubGroup, int32_t, XLoadL2>(g, (const int32_t*)(base + L.row_ptr), (const int32_t*)(base + L.col),
+                                          (const float*)(base + L.val), XLoadL2{(const float*)(base + L.x)},
                                           (float*)(base + L.y), rows, 1, c);
         }
       }

@@ -249,6 +249,7 @@ struct sg_ctx {
 
 static void ctx_free(sg_ctx* c) {
   if (!c) return;
+  tex_windows_remove(c);
   for (auto s : c->slots) if (s) cudaStreamDestroy(s);
   for (auto e : c->slot_ev) if (e) cudaEventDestroy(e);
   if (c->ctrl) cudaStreamDestroy(c->ctrl);
@@ -360,6 +361,7 @@ extern "C" int sg_init(sg_ctx** out, void* dev_pool, uint64_t pool_bytes, const 
     ctx_free(c);
     return rc;
   }
+  tex_windows_add(c, c->pool, c->pool_bytes);
   *out = c;
   return SG_OK;
 }

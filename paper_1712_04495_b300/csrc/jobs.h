@@ -16,6 +16,11 @@ struct GemmLayout {
 };
 
 int num_sms();
+// texture windows over a context's pool (the SpMV's x gathers): registered
+// by sg_init, removed before the context is freed; failures leave the pool
+// without windows (the kernels then gather with loads)
+void tex_windows_add(const void* owner, const void* base, uint64_t bytes);
+void tex_windows_remove(const void* owner);
 SpmvLayout spmv_layout(uint64_t rows, uint64_t nnz);
 GemmLayout gemm_layout(uint64_t m, uint64_t n, uint64_t k);
 

@@ -16,7 +16,8 @@ the device engine's replay (one warp, logical clock) of the same trace.
 
 The inputs are built by the library's own generators first (one launch per
 generator kernel), then the kernel runs `launches` times (default 3) on the
-current stream. Prints the CUDA-event time per launch.
+current stream. Prints the CUDA-event time per launch. The SpMV cases place
+the matrix in the grant of a scheduler pool, where an SpMV job's matrix is.
 """
 from __future__ import annotations
 
@@ -61,27 +62,41 @@ def run(kind: str, size: int | None = None, launches: int = 3, tile: str | None 
         lay = tg.spmv_layout(rows, cap)
         base = torch.empty(lay["total"], dtype=torch.uint8, device="cuda")
         tab = torch.from_numpy(tg.poisson_cdf_table(lam).view(np.int64).copy()).cuda()
-        p = base.data_ptr()
-        gen = lambda: abi.sg_gen_spmv(p, rows, cap, tab.data_ptr(), 5, 0, st)  # noqa: E731
-        gen()
-        torch.cuda.synchronize()
-        if kind == "fill":
-            ms = _time(gen, launches)
-            return {"kernel": "spmv generator", "rows": rows, "ms": ms}
-        ptr_t = torch.int64 if lay["ptr64"] else torch.int32
-        esz = 8 if lay["ptr64"] else 4
-        nnz = int(base[lay["row_ptr"] + esz * rows:lay["row_ptr"] + esz * (rows + 1)].view(ptr_t).item())
-        if kind == "gather":
-            assert abi.sg_spmv(p + lay["row_ptr"], lay["ptr64"], p + lay["col"], p + lay["val"],
-                               p + lay["x"], p + lay["y"], rows, st) == 0
-            out = torch.empty((nnz + 1023) // 1024, dtype=torch.float32, device="cuda")
-            ms = _time(lambda: abi.sg_gather_sum(p + lay["col"], p + lay["x"], nnz, out.data_ptr(), st), launches)
-            return {"kernel": "gather", "rows": rows, "nnz": nnz, "ms": ms, "gathers_per_s": nnz / (ms * 1e-3)}
-        ms = _time(lambda: abi.sg_spmv(p + lay["row_ptr"], lay["ptr64"], p + lay["col"], p + lay["val"],
-                                       p + lay["x"], p + lay["y"], rows, st), launches)
-        alg = esz * (rows + 1) + 8 * nnz + 8 * rows
-        return {"kernel": "spmv", "rows": rows, "nnz": nnz, "ms": ms, "alg_bytes": alg,
-                "gbs": alg / (ms * 1e-3) / 1e9}
+        # the matrix in the grant of a scheduler pool, as an SpMV job's is
+        # (x is then gathered through the pool's texture window)
+        from . import runtime
+        sched = runtime.Scheduler(lay["total"], pool=base)
+        try:
+            t = sched.declare(lay["total"])
+            rc, grant = sched.wait(t, 10 ** 9)
+            assert rc == abi.SG_OK, rc
+            p = base.data_ptr() + grant.offset
+            path = "texture" if abi.sg_spmv_gather_path(p + lay["x"], rows) == abi.SG_GATHER_TEXTURE else "loads"
+            gen = lambda: abi.sg_gen_spmv(p, rows, cap, tab.data_ptr(), 5, 0, st)  # noqa: E731
+            gen()
+            torch.cuda.synchronize()
+            if kind == "fill":
+                ms = _time(gen, launches)
+                return {"kernel": "spmv generator", "rows": rows, "ms": ms}
+            ptr_t = torch.int64 if lay["ptr64"] else torch.int32
+            esz = 8 if lay["ptr64"] else 4
+            nnz = int(base[lay["row_ptr"] + esz * rows:lay["row_ptr"] + esz * (rows + 1)].view(ptr_t).item())
+            if kind == "gather":
+                assert abi.sg_spmv(p + lay["row_ptr"], lay["ptr64"], p + lay["col"], p + lay["val"],
+                                   p + lay["x"], p + lay["y"], rows, st) == 0
+                out = torch.empty((nnz + 1023) // 1024, dtype=torch.float32, device="cuda")
+                ms = _time(lambda: abi.sg_gather_sum(p + lay["col"], p + lay["x"], rows, nnz, out.data_ptr(), st),
+                           launches)
+                return {"kernel": "gather", "rows": rows, "nnz": nnz, "ms": ms, "x_gathers": path,
+                        "gathers_per_s": nnz / (ms * 1e-3)}
+            ms = _time(lambda: abi.sg_spmv(p + lay["row_ptr"], lay["ptr64"], p + lay["col"], p + lay["val"],
+                                           p + lay["x"], p + lay["y"], rows, st), launches)
+            alg = esz * (rows + 1) + 8 * nnz + 8 * rows
+            return {"kernel": "spmv", "rows": rows, "nnz": nnz, "ms": ms, "alg_bytes": alg, "x_gathers": path,
+                    "gbs": alg / (ms * 1e-3) / 1e9}
+        finally:
+            torch.cuda.synchronize()
+            sched.shutdown()
     if kind == "triad":
         n = size or (64 << 20)
         buf = torch.empty(3 * n, dtype=torch.float32, device="cuda")

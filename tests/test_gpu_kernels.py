@@ -118,12 +118,12 @@ def test_gather_sum_matches_numpy(n):
     chunks = (n + 1023) // 1024
     d_col, d_x = torch.from_numpy(col).cuda(), torch.from_numpy(x).cuda()
     out = torch.full((chunks,), float("nan"), dtype=torch.float32, device="cuda")
-    assert abi.sg_gather_sum(d_col.data_ptr(), d_x.data_ptr(), n, out.data_ptr()) == 0
+    assert abi.sg_gather_sum(d_col.data_ptr(), d_x.data_ptr(), rows, n, out.data_ptr()) == 0
     got = out.cpu().numpy().astype(np.float64)
     ref = np.array([x[col[c * 1024:(c + 1) * 1024]].astype(np.float64).sum() for c in range(chunks)])
     mag = np.array([np.abs(x[col[c * 1024:(c + 1) * 1024]]).astype(np.float64).sum() for c in range(chunks)])
     assert np.all(np.abs(got - ref) <= 1e-5 * mag + 1e-30)
-    assert abi.sg_gather_sum(d_col.data_ptr() + 4, d_x.data_ptr(), n, out.data_ptr()) == abi.SG_ERR_INVALID
+    assert abi.sg_gather_sum(d_col.data_ptr() + 4, d_x.data_ptr(), rows, n, out.data_ptr()) == abi.SG_ERR_INVALID
 
 
 def _gemm(M, N, Kd, key, tile=None):
