@@ -361,12 +361,13 @@ def kernel_roofline(torch, abi, runtime, peaks):
     out["spmv"] = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                    "frac": gbs / peaks["hbm_gbs"], "traffic": profiled_traffic("spmv_csr_1e7rows_poisson16"),
                    "ms": ms,
-                   "kernel": "k_spmv<int> rows=1e7 nnz/row~Poisson(16)", "bytes_per_launch": alg,
+                   "kernel": f"k_spmv<int, {'XTex' if gather_path == abi.SG_GATHER_TEXTURE else 'XLoad'}> rows=1e7 "
+                             "nnz/row~Poisson(16)", "bytes_per_launch": alg,
                    "x_gathers": gpath,
                    "target": 0.70, "target_met": gbs / peaks["hbm_gbs"] >= 0.70,
                    "why_not": "each non-zero gathers x[col] at a uniform random column of a 40 MB x: one 32-byte "
-                              "L1/L2 sector per 4-byte value (l1tex__t_sector_hit_rate 6.7%); the kernel runs at "
-                              "the L1/L2 sector rate of random gathers, with HBM traffic equal to the "
+                              "L2 sector per 4-byte value (texture hit rate 0%); the kernel keeps the SM-to-crossbar "
+                              "request path 94% busy (97% for the gathers alone), with HBM traffic equal to the "
                               "algorithmic bytes",
                    "gathers_per_s": nnz / (ms * 1e-3),
                    "gather_ceiling": {"gathers_per_s": nnz / (g_ms * 1e-3), "ms": g_ms,
@@ -1122,8 +1123,9 @@ def main():
             extra["batching"] = batching_section(torch, abi, runtime)
             extra["serving"] = serving_section(torch, abi, runtime, args.serving_requests)
             extra["configs"] = configs_section(torch, abi, runtime)
-        # the kernel with the largest share of a step's ncu launch list is the
-        # CSR SpMV (30.8% of a step's kernel time), just ahead of the GEMM (28.9%)
+        # the single kernel with the largest share of a step's ncu launch list
+        # is the CSR SpMV (28.8% of a step's kernel time); the GEMM's 256 x 256
+        # tile has 26.9% (30.0% over all its tiles), reported in kernels.gemm
         extra["roofline"] = {k: kr["spmv"][k] for k in ("bound", "achieved", "peak", "unit", "frac",
                                                         "traffic")}
         extra["roofline"]["kernel"] = kr["spmv"]["kernel"]
@@ -1131,7 +1133,8 @@ def main():
         extra["roofline"]["target"] = kr["spmv"]["target"]
         extra["roofline"]["target_met"] = kr["spmv"]["target_met"]
         extra["roofline"]["gather_ceiling"] = kr["spmv"]["gather_ceiling"]
-        extra["roofline"]["note"] = ("below the 0.70 target: bound by random x gathers (L1/L2 sector rate), not "
+        extra["roofline"]["note"] = ("below the 0.70 target: bound by random x gathers (SM-to-crossbar request "
+                                     "rate), not "
                                      "by HBM; HBM traffic equals the algorithmic bytes; gather_ceiling is the "
                                      "same gathers alone, measured in this run (spmv_frac = the SpMV's fraction "
                                      "of that rate); kernels.gemm has the tcgen05 GEMM")
