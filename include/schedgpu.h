@@ -156,8 +156,12 @@ typedef struct sg_run_stats {
  * whose engine state -- budget, used bytes, per-ticket grants, the wait
  * queue and the free-extent list: the shared data of Sec. III-B -- lives in
  * device memory allocated here, once. dev_pool: device pointer, 256-byte
- * aligned, pool_bytes long (at most 2^47 granules), owned by the caller.
- * cfg may be NULL for defaults. *out receives the context. Errors:
+ * aligned, pool_bytes long (at most 2^47 granules), owned by the caller,
+ * who keeps it allocated until sg_shutdown. When dev_pool is aligned to the
+ * device's texture alignment (512 bytes), texture windows are made over the
+ * pool for the SpMV's x gathers (1-D textures, no device memory); they go
+ * with the context. cfg may be NULL for defaults. *out receives the
+ * context. Errors:
  * SG_ERR_INVALID (null/misaligned/oversized pool, bad config), SG_ERR_CUDA. */
 int sg_init(sg_ctx** out, void* dev_pool, uint64_t pool_bytes, const sg_config* cfg);
 
