@@ -554,14 +554,17 @@ int sg_gen_triad(float* b, float* c, uint64_t n, uint64_t key, void* stream);
  * Square matrix; device pointers. When x lies inside the pool of a live
  * context (as it does for SpMV jobs, whose arrays sit in their grant), x is
  * gathered through a texture window over that pool, otherwise with global
- * loads; y is the same either way. */
+ * loads; y is the same either way. A launch into a stream that is capturing
+ * a CUDA graph always uses loads, so that the graph holds no texture of a
+ * context and stays valid after sg_shutdown. */
 int sg_spmv(const void* row_ptr, int ptr64, const int32_t* col, const float* val,
             const float* x, float* y, uint64_t rows, void* stream);
 
 /* How sg_spmv (and every SpMV job) gathers an x of `rows` floats at device
- * address x: SG_GATHER_TEXTURE through a texture window of a live context's
- * pool, SG_GATHER_LOAD with global loads (x outside every pool, in a pool
- * whose base is not texture-aligned, or too long for one window). */
+ * address x when its stream is not capturing a graph: SG_GATHER_TEXTURE
+ * through a texture window of a live context's pool, SG_GATHER_LOAD with
+ * global loads (x outside every pool, in a pool whose base is not
+ * texture-aligned, or too long for one window). */
 #define SG_GATHER_LOAD    0
 #define SG_GATHER_TEXTURE 1
 int sg_spmv_gather_path(const float* x, uint64_t rows);
@@ -629,7 +632,8 @@ int sg_gen_gemm(uint16_t* A, uint16_t* Bt, uint32_t M, uint32_t N, uint32_t K, u
  * c; col (int32, n entries, 16-byte aligned, every entry in [0, x_len)),
  * x (fp32, x_len entries) and out_dev are device arrays owned by the
  * caller. x is gathered the way sg_spmv gathers it (a texture window when x
- * lies in a live context's pool, else loads). SG_ERR_INVALID for a null or
+ * lies in a live context's pool and the stream is not capturing, else
+ * loads). SG_ERR_INVALID for a null or
  * misaligned col, a null x or out_dev. */
 int sg_gather_sum(const int32_t* col, const float* x, uint64_t x_len, uint64_t n, float* out_dev,
                   void* stream);

@@ -248,6 +248,21 @@ void tex_windows_remove(const void* owner) {
 }
 
 // The window holding x[0, n), if any: the texture and x's first element in it.
+static bool tex_window_for(const float* x, uint64_t n, XTex* out);
+
+// The texture window for a launch on stream st. A launch into a stream that
+// is capturing a CUDA graph gathers with loads: the graph would otherwise
+// hold the context's texture objects, which die with the context, while the
+// graph may be launched after it.
+static bool launch_window(const float* x, uint64_t n, cudaStream_t st, XTex* out) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return cs == cudaStreamCaptureStatusNone && tex_window_for(x, n, out);
+}
+
 static bool tex_window_for(const float* x, uint64_t n, XTex* out) {
   const uintptr_t a = (uintptr_t)x;
   if (a & 3u) return false;
@@ -285,7 +300,7 @@ int launch_spmv(const void* row_ptr, int ptr64, const int32_t* col, const float*
   int vec = aligned16(col) && aligned16(val);
   unsigned grid = grid_for(rows, kSpmvRowsChunk);
   XTex xt;
-  if (tex_window_for(x, rows, &xt)) {
+  if (launch_window(x, rows, st, &xt)) {
     if (ptr64)
       k_spmv<int64_t, XTex><<<grid, kChunkThreads, 0, st>>>((const int64_t*)row_ptr, col, val, xt, y, rows, vec, h);
     else
@@ -481,7 +496,7 @@ extern "C" int sg_gather_sum(const int32_t* col, const float* x, uint64_t x_len,
   if (!col || !x || !out_dev || ((uintptr_t)col & 15u)) return SG_ERR_INVALID;
   const unsigned grid = grid_for(n, kGatherChunk);
   XTex xt;
-  if (tex_window_for(x, x_len, &xt))
+  if (launch_window(x, x_len, (cudaStream_t)stream, &xt))
     k_gather_sum<XTex><<<grid, kChunkThreads, 0, (cudaStream_t)stream>>>(col, xt, n, out_dev);
   else
     k_gather_sum<XLoad><<<grid, kChunkThreads, 0, (cudaStream_t)stream>>>(col, XLoad{x}, n, out_dev);

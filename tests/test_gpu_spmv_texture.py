@@ -146,3 +146,36 @@ def test_gather_sum_texture_equals_loads():
         assert torch.equal(o1.view(torch.int32), o2.view(torch.int32))
     finally:
         s.shutdown()
+
+
+def test_spmv_captured_in_a_graph_uses_loads():
+    """An SpMV captured into a CUDA graph must not hold a context's texture
+    objects (they die with the context): on a capturing stream it gathers
+    with loads. The replayed graph gives the same y as the texture path."""
+    abi, runtime = _mods()
+    rows, lam, key = 100_003, 16.0, 77
+    cap = tg.spmv_nnz_cap(rows, lam)
+    total = tg.spmv_layout(rows, cap)["total"]
+    pool = torch.zeros(total + 4096, dtype=torch.uint8, device="cuda")
+    s = runtime.Scheduler(total + 4096, pool=pool)
+    try:
+        bp = pool.data_ptr()
+        lay, table = _gen_in(bp, rows, lam, key)
+        assert abi.sg_spmv_gather_path(bp + lay["x"], rows) == abi.SG_GATHER_TEXTURE
+        args = (bp + lay["row_ptr"], False, bp + lay["col"], bp + lay["val"], bp + lay["x"], bp + lay["y"], rows)
+        assert abi.sg_spmv(*args) == 0
+        torch.cuda.synchronize()
+        y_tex = pool[lay["y"]:lay["y"] + 4 * rows].clone()
+        pool[lay["y"]:lay["y"] + 4 * rows].fill_(0xFF)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            assert abi.sg_spmv(*args, torch.cuda.current_stream().cuda_stream) == 0
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(pool[lay["y"]:lay["y"] + 4 * rows], y_tex)
+        y, mag = K.spmv(key, rows, table)
+        gy = y_tex.view(torch.float32).cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(gy - y) <= 1e-5 * mag + 1e-30)
+        del g
+    finally:
+        s.shutdown()
