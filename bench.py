@@ -552,7 +552,10 @@ def serving_section(torch, abi, runtime, requests: int, rates=(1000, 2000, 5000,
     of arrivals at that count, so they run `short_requests` (nothing waits at
     those rates either way). `overlap` repeats two rates with the runner
     starting SpMV and GEMM jobs side by side, also at `short_requests`."""
-    out = {"requests_per_rate": {}, "pool_gib": 64, "policy": "first_fit", "rates": {}, "overlap": {}}
+    out = {"requests_per_rate": {}, "pool_gib": 64, "policy": "first_fit", "rates": {}, "overlap": {},
+           "note": f"{requests} requests per rate from 5k req/s up; 1k and 2k req/s run {short_requests} (at "
+                   f"{requests} they would take {requests // 1000} s and {requests // 2000} s of arrivals, and "
+                   "nothing waits at those rates); overlap: the runner starting SpMV and GEMM jobs side by side"}
     pool = torch.empty(64 << 30, dtype=torch.uint8, device="cuda")
     for run_flags, rs, key in ((0, rates, "rates"), (abi.SG_RUNF_OVERLAP, overlap_rates, "overlap")):
         s = runtime.Scheduler(64 << 30, "first_fit", pool=pool, run_flags=run_flags)

@@ -47,6 +47,27 @@ def test_gather_path_follows_the_windows():
     assert abi.sg_spmv_gather_path(p, 1000) == abi.SG_GATHER_LOAD        # windows gone with the context
 
 
+def test_windows_of_two_contexts():
+    """Each live context's pool has its own windows; shutting one context
+    down leaves the other's."""
+    abi, runtime = _mods()
+    a = torch.empty(64 * MiB, dtype=torch.uint8, device="cuda")
+    b = torch.empty(64 * MiB, dtype=torch.uint8, device="cuda")
+    sa = runtime.Scheduler(64 * MiB, pool=a)
+    sb = runtime.Scheduler(64 * MiB, pool=b)
+    try:
+        T, L = abi.SG_GATHER_TEXTURE, abi.SG_GATHER_LOAD
+        assert abi.sg_spmv_gather_path(a.data_ptr() + 4096, 1000) == T
+        assert abi.sg_spmv_gather_path(b.data_ptr() + 4096, 1000) == T
+        sa.shutdown()
+        assert abi.sg_spmv_gather_path(a.data_ptr() + 4096, 1000) == L
+        assert abi.sg_spmv_gather_path(b.data_ptr() + 4096, 1000) == T
+    finally:
+        sa.shutdown()
+        sb.shutdown()
+    assert abi.sg_spmv_gather_path(b.data_ptr() + 4096, 1000) == abi.SG_GATHER_LOAD
+
+
 def test_pool_without_texture_alignment_uses_loads():
     abi, runtime = _mods()
     big = torch.empty(64 * MiB + 512, dtype=torch.uint8, device="cuda")
