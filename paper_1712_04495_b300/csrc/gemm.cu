@@ -135,13 +135,18 @@ __global__ void __launch_bounds__(TileCfg<BM, BN>::kThreads, 1)
       for (uint32_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
         uint32_t m, n;
         tile_coords(t, mt, nt, m, n);
+        // Round t / gridDim.x of the grid: the odd rounds walk K backwards, so
+        // that a round starts on the K slices of the band's A that the round
+        // before loaded last and L2 still holds
+        const bool back = ((t / gridDim.x) & 1u) != 0;
         for (uint32_t kb = 0; kb < kb_n; kb++) {
           if (!mbar_wait(smem_u32(&bar_empty[stage]), phase ^ 1u, &s_abort)) { ok = false; break; }
           const uint32_t sa = ring + stage * kStageBytes;
           const uint32_t fb = smem_u32(&bar_full[stage]);
+          const int32_t kx = (int32_t)((back ? kb_n - 1 - kb : kb) * kBK);
           mbar_expect_tx(fb, kStageBytes);
-          tma_load_2d(sa, &map_a, (int32_t)(kb * kBK), (int32_t)(m * BM), fb);
-          tma_load_2d(sa + kABytes, &map_b, (int32_t)(kb * kBK), (int32_t)(n * BN), fb);
+          tma_load_2d(sa, &map_a, kx, (int32_t)(m * BM), fb);
+          tma_load_2d(sa + kABytes, &map_b, kx, (int32_t)(n * BN), fb);
           if (++stage == kStages) { stage = 0; phase ^= 1u; }
         }
       }
@@ -167,7 +172,7 @@ __global__ void __launch_bounds__(TileCfg<BM, BN>::kThreads, 1)
 #pragma unroll
             for (uint32_t h = 0; h < (uint32_t)Cfg::kHalves; h++)   // rows h*128.. of A, one B tile
               mma_bf16(d + h * BN, smem_desc_sw128(sa + h * (128u * 128u) + kk * 32),
-                       smem_desc_sw128(sb + kk * 32), kIdesc, (kb | kk) != 0);
+                       smem_desc_sw128(sb + kk * 32), kIdesc, (kb | kk) != 0);   // the first issued starts it
           }
           mma_commit(smem_u32(&bar_empty[stage]));   // frees the stage when the MMAs finish
           if (++stage == kStages) { stage = 0; phase ^= 1u; }
