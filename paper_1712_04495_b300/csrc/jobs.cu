@@ -7,6 +7,7 @@
 #include <vector>
 #include "engine.cuh"
 #include "jobs.h"
+#include "texwin.h"
 #include "tiles.cuh"
 
 namespace sg {
@@ -176,15 +177,14 @@ static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 // ----------------------------------------------- texture windows over pools
 // The SpMV gathers x through the texture path when x lies in a pool that a
 // context registered: on a B300 that path sustains about 8% more random
-// 4-byte gathers per second than the load path. A 1-D texture over linear
-// memory spans at most cudaDevAttrMaxTexture1DLinearWidth elements (2^28
-// floats, 1 GiB, on a B300), so a pool is covered by windows of that size
-// starting every half window: an array of at most half a window lies wholly
-// inside one of them. Arrays outside every window (or larger) use loads.
+// 4-byte gathers per second than the load path. The windows' geometry (1 GiB
+// windows every 512 MiB on a B300) is texwin.h's; arrays outside every
+// window use loads.
 struct TexPool {
   const void* owner = nullptr;
   uintptr_t lo = 0;
-  uint64_t bytes = 0, win = 0, step = 0;
+  uint64_t bytes = 0;
+  TexWinLayout L;
   std::vector<cudaTextureObject_t> tex;
 };
 static std::mutex g_tex_mu;
@@ -197,31 +197,25 @@ static void tex_destroy(TexPool& P) {
 
 void tex_windows_add(const void* owner, const void* base, uint64_t bytes) {
   int dev = 0, maxw = 0, align = 0;
-  if (!base || bytes < 4 || cudaGetDevice(&dev) != cudaSuccess ||
+  if (!base || cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxTexture1DLinearWidth, dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&align, cudaDevAttrTextureAlignment, dev) != cudaSuccess) {
     cudaGetLastError();
     return;
   }
-  if (maxw < (1 << 16) || align <= 0 || ((uintptr_t)base % (uintptr_t)align)) return;
-  uint64_t welems = 1ull << 16;
-  while (welems * 2 <= (uint64_t)maxw && welems < (1ull << 30)) welems *= 2;
+  if (maxw <= 0 || align <= 0 || ((uintptr_t)base % (uintptr_t)align)) return;
   TexPool P;
   P.owner = owner;
   P.lo = (uintptr_t)base;
   P.bytes = bytes;
-  P.win = 4 * welems;
-  P.step = P.win / 2;
-  if (P.step % (uint64_t)align) return;
-  const uint64_t n = bytes <= P.win ? 1 : (bytes - P.win + P.step - 1) / P.step + 1;
-  for (uint64_t i = 0; i < n; i++) {
-    const uint64_t w0 = i * P.step, sz = (bytes - w0 < P.win ? bytes - w0 : P.win) & ~3ull;
+  P.L = texwin_layout(bytes, (uint64_t)maxw, (uint64_t)align);
+  for (uint64_t i = 0; i < P.L.count; i++) {
     cudaResourceDesc rd;
     memset(&rd, 0, sizeof rd);
     rd.resType = cudaResourceTypeLinear;
-    rd.res.linear.devPtr = (char*)base + w0;
+    rd.res.linear.devPtr = (char*)base + texwin_start(P.L, i);
     rd.res.linear.desc = cudaCreateChannelDesc<float>();
-    rd.res.linear.sizeInBytes = sz;
+    rd.res.linear.sizeInBytes = texwin_size(P.L, bytes, i);
     cudaTextureDesc td;
     memset(&td, 0, sizeof td);
     td.readMode = cudaReadModeElementType;
@@ -233,6 +227,7 @@ void tex_windows_add(const void* owner, const void* base, uint64_t bytes) {
     }
     P.tex.push_back(t);
   }
+  if (P.tex.empty()) return;
   std::lock_guard<std::mutex> g(g_tex_mu);
   g_tex_pools.push_back(std::move(P));
 }
@@ -265,17 +260,15 @@ static bool launch_window(const float* x, uint64_t n, cudaStream_t st, XTex* out
 
 static bool tex_window_for(const float* x, uint64_t n, XTex* out) {
   const uintptr_t a = (uintptr_t)x;
-  if (a & 3u) return false;
   std::lock_guard<std::mutex> g(g_tex_mu);
   for (const TexPool& P : g_tex_pools) {
     if (a < P.lo || a - P.lo >= P.bytes) continue;
     const uint64_t off = a - P.lo;
-    uint64_t i = off / P.step;
-    if (i >= P.tex.size()) i = P.tex.size() - 1;
-    const uint64_t w0 = i * P.step, sz = P.bytes - w0 < P.win ? P.bytes - w0 : P.win;
-    if (n > sz / 4 || off - w0 > sz - 4 * n) return false;
-    out->tex = P.tex[i];
-    out->base = (int32_t)((off - w0) / 4);
+    if (n > (P.bytes >> 2)) return false;
+    const int64_t i = texwin_pick(P.L, P.bytes, off, 4 * n);
+    if (i < 0) return false;
+    out->tex = P.tex[(size_t)i];
+    out->base = (int32_t)((off - texwin_start(P.L, (uint64_t)i)) / 4);
     return true;
   }
   return false;
