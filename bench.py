@@ -1070,15 +1070,15 @@ def main():
         # policies side by side (same trace, same pool)
         ms = {"first_fit": statistics.median(s["makespan_ns"] for s in stats) / 1e6}
         fifo = runtime.Scheduler(trace.budget, "fifo", pool=sched.pool)
-        sched_fifo = [step(s=fifo) for _ in range(2)]
+        sched_fifo = [step(s=fifo) for _ in range(5)]
         fifo.shutdown()
         ms["fifo"] = statistics.median(s["makespan_ns"] for s in sched_fifo) / 1e6
         # the runner starting SpMV and GEMM jobs side by side (SG_RUNF_OVERLAP)
         for name, pol in (("first_fit_overlap", "first_fit"), ("fifo_overlap", "fifo")):
             ov = runtime.Scheduler(trace.budget, pol, pool=sched.pool, run_flags=abi.SG_RUNF_OVERLAP)
-            ms[name] = statistics.median(step(s=ov)["makespan_ns"] for _ in range(3)) / 1e6
+            ms[name] = statistics.median(step(s=ov)["makespan_ns"] for _ in range(5)) / 1e6
             ov.shutdown()
-        ser = [step(abi.SG_RUN_SATURATED | abi.SG_RUN_EXCLUSIVE) for _ in range(2)]
+        ser = [step(abi.SG_RUN_SATURATED | abi.SG_RUN_EXCLUSIVE) for _ in range(5)]
         ms["exclusive_serial"] = statistics.median(s["makespan_ns"] for s in ser) / 1e6
         extra["makespan_ms"] = ms
         extra["makespan_ratio_vs_serial"] = {k: ms[k] / ms["exclusive_serial"] for k in
