@@ -179,6 +179,21 @@ def test_gemm_every_tile(M, N, Kd, tile):
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-5
 
 
+@pytest.mark.parametrize("M,N,Kd,tile", [(2000, 2000, 1000, (128, 64)), (2000, 2000, 1000, (128, 128)),
+                                         (4100, 4100, 1000, (256, 256))])
+def test_gemm_backward_rounds(M, N, Kd, tile):
+    """More tiles than the grid has CTAs: the grid's odd rounds walk K
+    backwards (4, 2 and 2 rounds here), starting on the ragged last K block
+    (K = 1000 is 15 full blocks of 64 and one of 40)."""
+    abi = _abi()
+    key = 991 + M + Kd + tile[1]
+    A, Bt, C = _gemm(M, N, Kd, key, abi.gemm_tile(*tile))
+    ref = K.gemm(key, M, N, Kd)
+    got = C.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(got))
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-5
+
+
 def test_gemm_tile_choice():
     abi = _abi()
     assert abi.sg_gemm_tile(8192, 8192) == abi.gemm_tile(256, 256)
